@@ -1,0 +1,226 @@
+/*
+ * rt.h -- C ABI of the GB300 formal-solution library (librt.so).
+ *
+ * The library solves the 3D radiative-transfer formal solution of Udnaes & Pereira (2023,
+ * arXiv:2306.01041) on two kinds of grid:
+ *   - a regular Cartesian grid, by plane-to-plane short characteristics (Sect. 2.6, after
+ *     Kunasz & Auer 1988), swept plane by plane;
+ *   - an irregular (Voronoi) grid, by transport along Delaunay lines from the two upwind
+ *     neighbours that best match each ray (Sect. 2.5, Eq. 5 and the weight formula after it),
+ *     swept in per-direction dependency levels;
+ * integrating the source function linearly across each optical-depth interval (Sect. 2.5,
+ * Eq. 2), accumulating J over angles (Sect. 2.1, Eq. 4), and closing each Lambda iteration with
+ * statistical equilibrium of a 2 + 1 level hydrogen-like atom (Sect. 2.2, Table 1).
+ *
+ * Conventions for every call
+ *   - Field arrays are device pointers owned by the caller, FP32, layout [nlam][npt], with
+ *     npt = nx*ny*nz (x fastest, then y, then z) on a regular grid or the site index on a
+ *     Voronoi grid.  They must be 16-byte aligned, else RT_EINVAL.
+ *   - The library owns the grid tables and the scratch it allocates for a grid.
+ *   - Calls are asynchronous on the given CUDA stream (NULL = legacy default stream), except
+ *     rt_grid_create and rt_lambda_iterate, which synchronise on their stream.
+ *   - No call aborts.  Errors come back as rt_status; rt_last_error() returns a message for the
+ *     calling host thread.  Device-side failures (a non-finite value, an exhausted wait) are
+ *     recorded in a device error word and surfaced by the next synchronising call.
+ *   - Directions: ndir unit vectors (mu_x, mu_y, mu_z), none with mu_z = 0, with weights wdir
+ *     summing to 1; J = sum_d wdir[d] I_d (Sect. 2.5, fixed-angle quadrature).
+ *   - Boundary conditions (the paper leaves them open; see rt_bc):
+ *       RT_BC_THERMAL: rays entering through the bottom wall carry I = S there; through the top
+ *                      wall, I = 0.
+ *       RT_BC_ZERO:    I = 0 on both walls.
+ *       RT_BC_ARRAY:   the caller supplies the entering intensity I_bc[ndir][nlam][nb] on the
+ *                      wall each direction enters through (nb = nx*ny on a regular grid, in
+ *                      x-fastest order; nb = nsites on a Voronoi grid, the value taken by a site
+ *                      whose upwind line starts at the wall).
+ */
+#ifndef RT_H
+#define RT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rt_grid *rt_grid_t;
+
+typedef enum {
+    RT_OK = 0,
+    RT_EINVAL = 1,     /* bad argument, size or alignment */
+    RT_ENOMEM = 2,     /* device or host allocation failed */
+    RT_ECUDA = 3,      /* a CUDA call failed */
+    RT_ECYCLE = 4,     /* Voronoi upwind links do not form a DAG */
+    RT_ETIMEOUT = 5,   /* a bounded device wait gave up */
+    RT_ENAN = 6,       /* a non-finite value was produced */
+    RT_ECAPACITY = 7,  /* a persistent launch cannot be co-resident */
+    RT_ENOCONV = 8     /* max_iter reached before the tolerance */
+} rt_status;
+
+enum rt_grid_kind { RT_GRID_REGULAR = 0, RT_GRID_VORONOI = 1 };
+enum rt_bc { RT_BC_THERMAL = 0, RT_BC_ZERO = 1, RT_BC_ARRAY = 2 };
+
+/* Grid description; every pointer is host memory, copied by rt_grid_create. */
+typedef struct {
+    int kind;                 /* RT_GRID_REGULAR or RT_GRID_VORONOI */
+    /* regular grid: uniform dx, dy; z[nz] strictly ascending (may be non-uniform) */
+    int nx, ny, nz;
+    double dx, dy;
+    const double *z;
+    /* Voronoi grid: sites and their Delaunay neighbours in CSR form.  nbr_idx[e] >= 0 is a
+     * site; -1-2k is the mirror image of site k in the bottom wall (z = box[4]) and -2-2k its
+     * mirror in the top wall (z = box[5]).  nbr_shift[e] = (sx+1)*3 + (sy+1) selects the
+     * periodic image (sx, sy in {-1,0,1}) of that neighbour; NULL means (0, 0) for all. */
+    int64_t nsites;
+    const double *xyz;        /* [nsites][3] */
+    const int64_t *nbr_off;   /* [nsites+1] */
+    const int32_t *nbr_idx;   /* [nbr_off[nsites]] */
+    const int8_t *nbr_shift;  /* [nbr_off[nsites]] or NULL */
+    double box[6];            /* x0, x1, y0, y1, z0, z1 */
+    int periodic_xy;          /* 1: periodic in x and y; 0: closed sides with zero inflow */
+    int ndir;                 /* number of quadrature directions, 1..64 */
+    const double *dirs;       /* [ndir][3] unit vectors */
+    const double *wdir;       /* [ndir] weights */
+    double r_exponent;        /* exponent r of the two-line weights (Sect. 2.5; paper: 7) */
+} rt_grid_desc;
+
+/* Builds a grid: validates the description, precomputes the regular-grid upwind stencils or the
+ * Voronoi upwind tables (two best-aligned upwind neighbours per site and direction, weights
+ * v^r / sum v^r, Delaunay segment lengths) and per-direction dependency levels, and uploads
+ * them.  Returns RT_ECYCLE if the Voronoi upwind links are not acyclic.  Synchronous. */
+rt_status rt_grid_create(const rt_grid_desc *desc, void *stream, rt_grid_t *out);
+void rt_grid_destroy(rt_grid_t grid);
+
+/* Host-side facts about a built grid.  Any output pointer may be NULL.
+ * npt: points/sites; ntop: points on the emergent layer (nx*ny, or the Voronoi sites whose
+ * neighbour list holds a top-wall mirror); max_levels: the largest number of dependency levels
+ * over the directions (nz on a regular grid); n_fallback: Voronoi (site, direction) pairs that
+ * had no upwind neighbour with v > 0 and took the most nearly vertical upwind neighbour. */
+rt_status rt_grid_info(rt_grid_t grid, int64_t *npt, int64_t *ntop, int *max_levels,
+                       int64_t *n_fallback);
+
+/* Copies the (site, direction) upwind tables to host arrays for inspection:
+ * k[ndir][nsites][2] (site, -1 bottom wall, -2 top wall), w[ndir][nsites][2],
+ * len[ndir][nsites][2] (metres), level[ndir][nsites].  Voronoi grids only.  Synchronous. */
+rt_status rt_grid_tables(rt_grid_t grid, int32_t *k, float *w, float *len, int32_t *level);
+
+/* Emergent-layer point indices (host array of ntop entries). */
+rt_status rt_grid_top_points(rt_grid_t grid, int64_t *idx);
+
+/* Formal solution (Eq. 2 along every ray of the quadrature) and J = sum_d w_d I_d (Eq. 4).
+ * alpha, S: [nlam][npt] device; J: [nlam][npt] device, overwritten.
+ * I_bc: device [ndir][nlam][nb] when bc == RT_BC_ARRAY, else ignored.
+ * I_dir: optional device [ndir][nlam][npt] receiving every directional intensity, or NULL. */
+rt_status rt_formal_solution(rt_grid_t grid, int nlam, const float *alpha, const float *S,
+                             int bc, const float *I_bc, float *J, float *I_dir, void *stream);
+
+/* ---- atom, source terms and the Lambda iteration (Sect. 2.1-2.2) --------------------------- */
+/* Model atom: levels 1, 2 and the continuum p (Table 1), line 1-2 with oscillator strength f,
+ * bound-free from 1 and from 2 (Kramers cross sections), a Voigt line profile with damping a
+ * and the Doppler width of the hydrogen mass, collisions C21 = q n_e T^-1/2 and
+ * C_ip = q n_e T^-1/2 exp(-E_ip/kT) (their inverses by detailed balance), and a grey background
+ * alpha_bg = kappa0 rho (T/5000)^9 with source function B.  Wavelength nodes lam[nlam] (m) with
+ * quadrature weights wlam[nlam] (m); kind[j] = 0 for a line node, 1 for the bound-free node of
+ * level 1, 2 for that of level 2 (each node feeds the rate integral of its kind). */
+typedef struct {
+    double E_cm[3];           /* level energies, cm^-1 (the third is the continuum edge) */
+    double g[3];              /* statistical weights */
+    double f_line;
+    double voigt_a;
+    double q_coll;            /* m^3 s^-1 K^1/2 */
+    double kappa0;            /* m^2 kg^-1 */
+    int nlam;
+    const double *lam;        /* host [nlam] */
+    const double *wlam;       /* host [nlam] */
+    const int32_t *kind;      /* host [nlam] */
+} rt_atom;
+
+/* Atmosphere on the grid's points: device FP32 arrays [npt]. */
+typedef struct {
+    const float *T, *rho, *ne, *nH;
+} rt_atmos;
+
+/* LTE continuum of the synthetic atmospheres: alpha = kappa0 rho (T/5000)^9, S = B_lam(T) in
+ * W m^-2 m^-1 sr^-1, at one wavelength lam (m).  alpha, S: device [npt]. */
+rt_status rt_source_terms_lte(int64_t npt, const float *T, const float *rho, double kappa0,
+                              double lam, float *alpha, float *S, void *stream);
+
+/* alpha, S [nlam][npt] of the atom from the populations pops [3][npt] (n1, n2, n_p). */
+rt_status rt_source_terms(rt_grid_t grid, const rt_atom *atom, const rt_atmos *atm,
+                          const float *pops, float *alpha, float *S, void *stream);
+
+/* Saha-Boltzmann (LTE) populations pops [3][npt], the starting point of the iteration. */
+rt_status rt_lte_populations(rt_grid_t grid, const rt_atom *atom, const rt_atmos *atm,
+                             float *pops, void *stream);
+
+/* Radiative + collisional rates from J [nlam][npt] and the statistical-equilibrium solution:
+ * pops [3][npt] is read (old) and overwritten (new); *dmax_dev (device float, may be NULL)
+ * receives max over points and levels of |n_new - n_old| / n_new. */
+rt_status rt_statistical_equilibrium(rt_grid_t grid, const rt_atom *atom, const rt_atmos *atm,
+                                     const float *J, float *pops, float *dmax_dev, void *stream);
+
+/* Lambda iteration (Sect. 2.1, Eq. 3-4): pops [3][npt] device, in = start (e.g. LTE),
+ * out = last iterate.  Iterates source terms -> formal solution (RT_BC_THERMAL) -> rates ->
+ * statistical equilibrium until max |dn/n| < tol or max_iter iterations (RT_ENOCONV then).
+ * iters_out (host, may be NULL); history (host [max_iter], may be NULL) gets max |dn/n| per
+ * iteration.  use_graph != 0 captures one iteration in a CUDA graph and replays it.
+ * Synchronises once per iteration to read the convergence scalar. */
+rt_status rt_lambda_iterate(rt_grid_t grid, const rt_atom *atom, const rt_atmos *atm,
+                            float *pops, int max_iter, double tol, int *iters_out,
+                            float *history, int use_graph, void *stream);
+
+/* ---- emergent intensity and its adjoint (Sect. 2.5-2.6; Eq. 2 differentiated) -------------- */
+/* Intensity along one direction dir[3] (mu_z > 0) at the emergent layer:
+ * I_top [nlam][ntop] (device).  Regular grid: the top plane.  Voronoi grid: the sites listed by
+ * rt_grid_top_points.  bc as for rt_formal_solution (RT_BC_ARRAY not accepted here). */
+rt_status rt_emergent_intensity(rt_grid_t grid, const double dir[3], int nlam,
+                                const float *alpha, const float *S, int bc, float *I_top,
+                                void *stream);
+
+/* Gradient of L = sum(gI_top * I_top) with respect to alpha and S at every point, for the
+ * emergent intensity above: g_alpha, g_S [nlam][npt] device, overwritten.  The forward
+ * intensities are kept only every ckpt_stride planes/levels (>= 1) and recomputed in between;
+ * ws is a device workspace of rt_adjoint_workspace_size bytes (16-byte aligned). */
+size_t rt_adjoint_workspace_size(rt_grid_t grid, int nlam, int ckpt_stride);
+rt_status rt_formal_solution_adjoint(rt_grid_t grid, const double dir[3], int nlam,
+                                     const float *alpha, const float *S, int bc,
+                                     const float *gI_top, float *g_alpha, float *g_S,
+                                     int ckpt_stride, void *ws, size_t ws_bytes, void *stream);
+
+/* Chain rule to temperature: g_T [npt] = sum_lam (g_alpha dalpha/dT + g_S dS/dT) with the
+ * populations held fixed (the atom's source terms, derivatives by forward-mode dual numbers). */
+rt_status rt_source_terms_adjoint(rt_grid_t grid, const rt_atom *atom, const rt_atmos *atm,
+                                  const float *pops, const float *g_alpha, const float *g_S,
+                                  float *g_T, void *stream);
+
+/* LTE continuum counterpart: g_T = g_alpha dalpha/dT + g_S dB/dT at one wavelength. */
+rt_status rt_source_terms_lte_adjoint(int64_t npt, const float *T, const float *rho,
+                                      double kappa0, double lam, const float *g_alpha,
+                                      const float *g_S, float *g_T, void *stream);
+
+/* ---- batched persistent sweep over several Voronoi grids ------------------------------------ */
+typedef struct rt_batch *rt_batch_t;
+
+/* A batch of Voronoi grids (same ndir) solved by one persistent level-scheduled launch.
+ * lam_chunk[b] (host, may be NULL for the built-in choice) is the wavelength chunk each work
+ * item of grid b carries; threads is the block size (0 = built-in). */
+rt_status rt_batch_create(const rt_grid_t *grids, int ngrids, int nlam, const int *lam_chunk,
+                          int threads, rt_batch_t *out);
+void rt_batch_destroy(rt_batch_t batch);
+
+/* Formal solution of every grid of the batch: alpha[b], S[b], J[b] are device [nlam][npt_b]. */
+rt_status rt_batch_formal_solution(rt_batch_t batch, const float *const *alpha,
+                                   const float *const *S, int bc, float *const *J,
+                                   void *stream);
+
+const char *rt_last_error(void);
+
+/* Host-only diagnostic: G(v) = 2 v F(v) - 1 (F = Dawson's integral) from the double-precision
+ * series that seeds the device Voigt tables; lets CPU tests check the tables' source. */
+double rt_debug_G_host(double v);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RT_H */

@@ -1,0 +1,11 @@
+"""GB300-native formal solution of 3D radiative transfer on regular and Voronoi grids
+(Udnaes & Pereira 2023, arXiv:2306.01041): a thin Python binding over librt.so.
+
+Build the library first (``python -c "import __graft_entry__ as g; g.build()"`` or
+``python paper_2306_01041_gb300/build.py``); importing the API raises if it is missing.
+"""
+from ._lib import (RT_BC_ARRAY, RT_BC_THERMAL, RT_BC_ZERO, RTError, lib)  # noqa: F401
+from .api import (Atmos, Atom, Batch, EmergentIntensity, Grid, RegularGrid,  # noqa: F401
+                  VoronoiGrid, emergent_intensity, formal_solution, formal_solution_adjoint,
+                  lambda_iterate, lte_populations, source_terms, source_terms_adjoint,
+                  source_terms_lte, source_terms_lte_adjoint, statistical_equilibrium)

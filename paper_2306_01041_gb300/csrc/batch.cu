@@ -1,0 +1,326 @@
+// Batched persistent sweep over several Voronoi grids of uneven size.
+//
+// Work item = (grid, wavelength chunk).  A block takes an item from a device queue and sweeps all
+// directions of that grid for its wavelengths, level by level, with one __syncthreads between
+// levels; J is summed in direction order by the same block, so the result is deterministic and no
+// block ever waits for another (no co-residency requirement, no device-side spin).  The grid is
+// sized to the number of blocks that fit at once (persistent), and items are queued largest
+// first.  Chunk sizes per grid balance the items' work (sites x chunk).
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+
+#include "device_common.cuh"
+#include "rt_impl.h"
+
+namespace rt {
+
+struct BatchGridDev {
+    const Upwind *up;          // [ndir][n] slot order
+    const int32_t *order;      // [ndir][n]
+    const int64_t *lvl;        // level offsets, all directions concatenated
+    const int32_t *lvl_base;   // [ndir + 1] start of each direction's offsets in lvl
+    const float *A, *S;        // [n][nlam] transposed inputs
+    float *I, *J;              // [n][nlam]
+    int n;
+};
+
+struct BatchItem {
+    int grid, c0, lc;
+    int pad;
+};
+
+struct BatchArgs {
+    const BatchGridDev *grids;
+    const BatchItem *items;
+    int *queue;
+    const float *wdir;         // [ndir]
+    const float *up_flag;      // [ndir] 1 for mu_z > 0
+    unsigned *err;
+    int nitems, ndir, nlam, bc;
+};
+
+__global__ void __launch_bounds__(512) batch_sweep_kernel(const BatchArgs a)
+{
+    __shared__ int item_s;
+    for (;;) {
+        if (threadIdx.x == 0) item_s = atomicAdd(a.queue, 1);
+        __syncthreads();
+        const int it = item_s;
+        __syncthreads();
+        if (it >= a.nitems) return;
+        const BatchItem item = a.items[it];
+        const BatchGridDev g = a.grids[item.grid];
+        for (int d = 0; d < a.ndir; ++d) {
+            const Upwind *up = g.up + (size_t)d * g.n;
+            const int32_t *order = g.order + (size_t)d * g.n;
+            const int b0 = g.lvl_base[d], b1 = g.lvl_base[d + 1];
+            const float w = a.wdir[d];
+            const bool upd = a.up_flag[d] > 0.f;
+            for (int L = b0; L + 1 < b1; ++L) {
+                const int64_t s0 = g.lvl[L], s1 = g.lvl[L + 1];
+                const int64_t work = (s1 - s0) * item.lc;
+                for (int64_t t = threadIdx.x; t < work; t += blockDim.x) {
+                    const int64_t slot = s0 + t / item.lc;
+                    const int l = item.c0 + (int)(t % item.lc);
+                    const Upwind u = up[slot];
+                    const int i = order[slot];
+                    const size_t il = (size_t)i * a.nlam + l;
+                    const float Si = __ldg(g.S + il), Ai = __ldg(g.A + il);
+                    float acc = 0.f;
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        const int k = c ? u.k2 : u.k1;
+                        const float wk = c ? 1.f - u.w1 : u.w1;
+                        const float len = c ? u.l2 : u.l1;
+                        if (wk == 0.f) continue;
+                        float Ik, Sk, Ak;
+                        if (k >= 0) {
+                            const size_t kl = (size_t)k * a.nlam + l;
+                            Ik = g.I[kl];
+                            Sk = __ldg(g.S + kl);
+                            Ak = __ldg(g.A + kl);
+                        } else {
+                            Sk = Si;
+                            Ak = Ai;
+                            Ik = (a.bc == RT_BC_THERMAL && upd && k == -1) ? Si : 0.f;
+                        }
+                        float ex, w0, w1;
+                        lin_weights(0.5f * (Ak + Ai) * len, ex, w0, w1);
+                        acc += wk * (Ik * ex + w0 * Sk + w1 * Si);
+                    }
+                    g.I[il] = acc;
+                    const float jv = d == 0 ? w * acc : g.J[il] + w * acc;
+                    if (!isfinite(jv)) flag_error(a.err, ERR_NAN);
+                    g.J[il] = jv;
+                }
+                __syncthreads();
+            }
+        }
+    }
+}
+
+__global__ void transpose_kernel_b(const float *__restrict__ in, float *__restrict__ out, int rows,
+                                   int cols)
+{
+    __shared__ float tile[32][33];
+    int c = blockIdx.x * 32 + threadIdx.x;
+    int r0 = blockIdx.y * 32;
+    for (int dr = threadIdx.y; dr < 32; dr += blockDim.y) {
+        int r = r0 + dr;
+        if (r < rows && c < cols) tile[dr][threadIdx.x] = in[(size_t)r * cols + c];
+    }
+    __syncthreads();
+    int r = r0 + threadIdx.x;
+    for (int dc = threadIdx.y; dc < 32; dc += blockDim.y) {
+        int cc = blockIdx.x * 32 + dc;
+        if (r < rows && cc < cols) out[(size_t)cc * rows + r] = tile[threadIdx.x][dc];
+    }
+}
+
+static void transpose_b(const float *in, float *out, int rows, int cols, cudaStream_t st)
+{
+    dim3 grid((cols + 31) / 32, (rows + 31) / 32);
+    transpose_kernel_b<<<grid, dim3(32, 8), 0, st>>>(in, out, rows, cols);
+}
+
+}  // namespace rt
+
+using namespace rt;
+
+struct rt_batch {
+    std::vector<rt_grid *> grids;
+    int nlam = 0, ndir = 0, threads = 512, blocks = 0;
+    std::vector<BatchItem> h_items;
+    BatchItem *d_items = nullptr;
+    BatchGridDev *d_grids = nullptr;
+    std::vector<BatchGridDev> h_grids;
+    int64_t *d_lvl = nullptr;
+    int32_t *d_lvl_base = nullptr;
+    float *d_wdir = nullptr, *d_upf = nullptr;
+    float *d_fields = nullptr;   // per grid A, S, I, J [n][nlam]
+    int *d_queue = nullptr;
+    unsigned *d_err = nullptr;
+    ~rt_batch()
+    {
+        cudaFree(d_items);
+        cudaFree(d_grids);
+        cudaFree(d_lvl);
+        cudaFree(d_lvl_base);
+        cudaFree(d_wdir);
+        cudaFree(d_upf);
+        cudaFree(d_fields);
+        cudaFree(d_queue);
+        cudaFree(d_err);
+    }
+};
+
+extern "C" {
+
+rt_status rt_batch_create(const rt_grid_t *grids, int ngrids, int nlam, const int *lam_chunk,
+                          int threads, rt_batch_t *out)
+{
+    if (!grids || ngrids < 1 || nlam < 1 || !out) return fail(RT_EINVAL, "bad argument");
+    *out = nullptr;
+    rt_batch *b = new (std::nothrow) rt_batch();
+    if (!b) return fail(RT_ENOMEM, "host allocation failed");
+    b->nlam = nlam;
+    b->ndir = grids[0]->ndir;
+    b->threads = threads > 0 ? threads : 512;
+    if (b->threads > 512 || b->threads % 32) {
+        delete b;
+        return fail(RT_EINVAL, "threads must be a multiple of 32 up to 512");
+    }
+    int64_t ntot = 0, nmin = INT64_MAX;
+    for (int i = 0; i < ngrids; ++i) {
+        rt_grid *g = grids[i];
+        if (!g || g->kind != RT_GRID_VORONOI || g->ndir != b->ndir) {
+            delete b;
+            return fail(RT_EINVAL, "batch grids must be Voronoi grids with the same directions");
+        }
+        for (int d = 0; d < g->ndir; ++d)
+            if (g->wdir[d] != grids[0]->wdir[d] || g->dirs[3 * d + 2] != grids[0]->dirs[3 * d + 2]) {
+                delete b;
+                return fail(RT_EINVAL, "batch grids must share the quadrature");
+            }
+        b->grids.push_back(g);
+        ntot += g->nsites;
+        nmin = std::min<int64_t>(nmin, g->nsites);
+    }
+    int dev = 0, nsm = 0, per_sm = 0;
+    RT_CUDA(cudaGetDevice(&dev));
+    RT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    RT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_sweep_kernel, b->threads, 0));
+    if (per_sm < 1) {
+        delete b;
+        return fail(RT_ECAPACITY, "the batched sweep kernel cannot be resident");
+    }
+    b->blocks = nsm * per_sm;
+    // items: default chunk sizes make every item carry about the same number of (site, lambda)
+    // pairs, about total / (2 * resident blocks)
+    for (int i = 0; i < ngrids; ++i) {
+        int lc;
+        if (lam_chunk) {
+            lc = lam_chunk[i];
+        } else {
+            const double target = (double)ntot * nlam / (2.0 * b->blocks);
+            lc = (int)std::lround(target / (double)grids[i]->nsites);
+        }
+        lc = std::max(1, std::min(nlam, lc));
+        for (int c0 = 0; c0 < nlam; c0 += lc)
+            b->h_items.push_back(BatchItem{i, c0, std::min(lc, nlam - c0), 0});
+    }
+    std::stable_sort(b->h_items.begin(), b->h_items.end(), [&](const BatchItem &x, const BatchItem &y) {
+        return (double)grids[x.grid]->nsites * x.lc > (double)grids[y.grid]->nsites * y.lc;
+    });
+    // device tables
+    std::vector<int64_t> lvl;
+    std::vector<int32_t> base;
+    std::vector<size_t> base_at(ngrids);
+    for (int i = 0; i < ngrids; ++i) {
+        base_at[i] = base.size();
+        for (int d = 0; d < b->ndir; ++d) {
+            base.push_back((int32_t)lvl.size());
+            const auto &o = grids[i]->vt.lvl_off[d];
+            lvl.insert(lvl.end(), o.begin(), o.end());
+        }
+        base.push_back((int32_t)lvl.size());
+    }
+    size_t fsz = 0;
+    for (int i = 0; i < ngrids; ++i) fsz += 4 * (size_t)grids[i]->nsites * nlam;
+    std::vector<float> wd(b->ndir), uf(b->ndir);
+    for (int d = 0; d < b->ndir; ++d) {
+        wd[d] = (float)grids[0]->wdir[d];
+        uf[d] = grids[0]->dirs[3 * d + 2] > 0 ? 1.f : 0.f;
+    }
+    cudaError_t e = cudaSuccess;
+#define BT(x)                                                   \
+    do {                                                        \
+        if (e == cudaSuccess) e = (x);                          \
+    } while (0)
+    BT(cudaMalloc(&b->d_items, b->h_items.size() * sizeof(BatchItem)));
+    BT(cudaMalloc(&b->d_grids, ngrids * sizeof(BatchGridDev)));
+    BT(cudaMalloc(&b->d_lvl, lvl.size() * sizeof(int64_t)));
+    BT(cudaMalloc(&b->d_lvl_base, base.size() * sizeof(int32_t)));
+    BT(cudaMalloc(&b->d_wdir, b->ndir * sizeof(float)));
+    BT(cudaMalloc(&b->d_upf, b->ndir * sizeof(float)));
+    BT(cudaMalloc(&b->d_fields, fsz * sizeof(float)));
+    BT(cudaMalloc(&b->d_queue, sizeof(int)));
+    BT(cudaMalloc(&b->d_err, sizeof(unsigned)));
+    if (e != cudaSuccess) {
+        delete b;
+        return cuda_fail(e, "batch allocation");
+    }
+    float *f = b->d_fields;
+    for (int i = 0; i < ngrids; ++i) {
+        rt_grid *g = grids[i];
+        const size_t m = (size_t)g->nsites * nlam;
+        BatchGridDev gd;
+        gd.up = g->vt.d_up;
+        gd.order = g->vt.d_order;
+        gd.lvl = b->d_lvl;
+        gd.lvl_base = b->d_lvl_base + base_at[i];
+        gd.A = f;
+        gd.S = f + m;
+        gd.I = f + 2 * m;
+        gd.J = f + 3 * m;
+        gd.n = (int)g->nsites;
+        f += 4 * m;
+        b->h_grids.push_back(gd);
+    }
+    BT(cudaMemcpy(b->d_items, b->h_items.data(), b->h_items.size() * sizeof(BatchItem),
+                  cudaMemcpyHostToDevice));
+    BT(cudaMemcpy(b->d_grids, b->h_grids.data(), ngrids * sizeof(BatchGridDev),
+                  cudaMemcpyHostToDevice));
+    BT(cudaMemcpy(b->d_lvl, lvl.data(), lvl.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+    BT(cudaMemcpy(b->d_lvl_base, base.data(), base.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    BT(cudaMemcpy(b->d_wdir, wd.data(), b->ndir * sizeof(float), cudaMemcpyHostToDevice));
+    BT(cudaMemcpy(b->d_upf, uf.data(), b->ndir * sizeof(float), cudaMemcpyHostToDevice));
+    BT(cudaMemset(b->d_err, 0, sizeof(unsigned)));
+#undef BT
+    if (e != cudaSuccess) {
+        delete b;
+        return cuda_fail(e, "batch upload");
+    }
+    *out = b;
+    return RT_OK;
+}
+
+void rt_batch_destroy(rt_batch_t b) { delete b; }
+
+rt_status rt_batch_formal_solution(rt_batch_t b, const float *const *alpha, const float *const *S,
+                                   int bc, float *const *J, void *stream)
+{
+    if (!b || !alpha || !S || !J) return fail(RT_EINVAL, "null argument");
+    if (bc != RT_BC_THERMAL && bc != RT_BC_ZERO) return fail(RT_EINVAL, "bc must be THERMAL or ZERO");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int ng = (int)b->grids.size();
+    for (int i = 0; i < ng; ++i) {
+        if (!alpha[i] || !S[i] || !J[i]) return fail(RT_EINVAL, "null field");
+        const BatchGridDev &g = b->h_grids[i];
+        transpose_b(alpha[i], const_cast<float *>(g.A), b->nlam, g.n, st);
+        transpose_b(S[i], const_cast<float *>(g.S), b->nlam, g.n, st);
+    }
+    RT_CUDA(cudaMemsetAsync(b->d_queue, 0, sizeof(int), st));
+    BatchArgs a;
+    a.grids = b->d_grids;
+    a.items = b->d_items;
+    a.queue = b->d_queue;
+    a.wdir = b->d_wdir;
+    a.up_flag = b->d_upf;
+    a.err = b->d_err;
+    a.nitems = (int)b->h_items.size();
+    a.ndir = b->ndir;
+    a.nlam = b->nlam;
+    a.bc = bc;
+    const int blocks = std::min<int>(b->blocks, a.nitems);
+    batch_sweep_kernel<<<blocks, b->threads, 0, st>>>(a);
+    for (int i = 0; i < ng; ++i) {
+        const BatchGridDev &g = b->h_grids[i];
+        transpose_b(g.J, J[i], g.n, b->nlam, st);
+    }
+    RT_CUDA(cudaGetLastError());
+    return RT_OK;
+}
+
+}  // extern "C"

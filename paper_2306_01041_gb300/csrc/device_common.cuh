@@ -1,0 +1,53 @@
+// Device helpers shared by the kernels of librt.so.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace rt {
+
+// Linear-S integration over one optical-depth interval d (Sect. 2.5: S linear across the
+// interval; Eq. 2):  I = I_up e^-d + w0 S_up + w1 S with e0 = 1 - e^-d, w1 = (d - e0) / d,
+// w0 = e0 - w1.  Below d = 0.1 the cancellation in d - e0 is avoided by the Taylor series of w1
+// (truncated after d^5, relative error < 1e-9 there); above, e0 comes from the fast exponential.
+__device__ __forceinline__ void lin_weights(float d, float &ex, float &w0, float &w1)
+{
+    ex = __expf(-d);
+    if (d < 0.1f) {
+        // w1 = d/2 - d^2/6 + d^3/24 - d^4/120 + d^5/720
+        w1 = d * (0.5f + d * (-1.0f / 6.0f + d * (1.0f / 24.0f + d * (-1.0f / 120.0f +
+                                                                     d * (1.0f / 720.0f)))));
+        // w0 = e0 - w1, e0 = d - d^2/2 + d^3/6 - d^4/24 + d^5/120
+        w0 = d * (0.5f + d * (-1.0f / 3.0f + d * (1.0f / 8.0f + d * (-1.0f / 30.0f +
+                                                                   d * (1.0f / 144.0f)))));
+    } else {
+        float e0 = 1.0f - ex;
+        w1 = 1.0f - e0 * __frcp_rn(d);
+        w0 = e0 - w1;
+    }
+}
+
+// d/dd of (e^-d, w0, w1), for the adjoint sweeps.
+__device__ __forceinline__ void lin_weights_deriv(float d, float ex, float &dex, float &dw0,
+                                                  float &dw1)
+{
+    dex = -ex;
+    if (d < 0.1f) {
+        // dw1/dd = 1/2 - d/3 + d^2/8 - d^3/30 + d^4/144
+        dw1 = 0.5f + d * (-1.0f / 3.0f + d * (1.0f / 8.0f + d * (-1.0f / 30.0f + d * (1.0f / 144.0f))));
+        // dw0/dd = e^-d - dw1/dd = 1/2 - 2d/3 + 3d^2/8 - 2d^3/15 + 5d^4/144
+        dw0 = 0.5f + d * (-2.0f / 3.0f + d * (3.0f / 8.0f + d * (-2.0f / 15.0f +
+                                                                d * (5.0f / 144.0f))));
+    } else {
+        float r = __frcp_rn(d);
+        float e0 = 1.0f - ex;
+        dw1 = (e0 - d * ex) * r * r;
+        dw0 = ex - dw1;
+    }
+}
+
+__device__ __forceinline__ void flag_error(unsigned *err, unsigned bit)
+{
+    if (err) atomicOr(err, bit);
+}
+
+}  // namespace rt

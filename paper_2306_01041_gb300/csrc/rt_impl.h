@@ -1,0 +1,142 @@
+// Internal declarations shared by the translation units of librt.so (host and device).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/rt.h"
+
+namespace rt {
+
+// ---- error reporting --------------------------------------------------------------------------
+rt_status fail(rt_status st, const std::string &msg);
+rt_status cuda_fail(cudaError_t e, const char *what);
+#define RT_CUDA(call)                                                 \
+    do {                                                              \
+        cudaError_t e_ = (call);                                      \
+        if (e_ != cudaSuccess) return ::rt::cuda_fail(e_, #call);     \
+    } while (0)
+#define RT_TRY(call)                                                  \
+    do {                                                              \
+        rt_status s_ = (call);                                        \
+        if (s_ != RT_OK) return s_;                                   \
+    } while (0)
+
+inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// device error word bits (rt::DevErr in the grid)
+enum : unsigned { ERR_NAN = 1u, ERR_TIMEOUT = 2u, ERR_INDEX = 4u };
+
+constexpr int MAX_DIR = 64;
+
+// ---- regular grid: per (plane, direction) upwind stencil ----------------------------------------
+// The upwind point of (i, j) in plane k lies at (i + ax + tx, j + ay + ty) of the upwind plane,
+// tx, ty in [0, 1).  Bilinear weights w[0..3] for corners (ax,ay), (ax+1,ay), (ax,ay+1),
+// (ax+1,ay+1); hds = half the path length between the planes (so dtau = (a_up + a) * hds).
+// axm, aym: ax, ay reduced modulo nx, ny (periodic wrap without integer division on the device).
+struct Stencil {
+    int ax, ay, axm, aym;
+    float w0, w1, w2, w3;
+    float hds;
+    float pad;
+};
+
+// ---- Voronoi grid: per (direction, site) upwind record --------------------------------------------
+// k1, k2: upwind site (>= 0) or wall (-1 bottom, -2 top); w1 (w2 = 1 - w1; w1 = 1 and w2 = 0
+// with a single upwind line); l1, l2: segment lengths.
+struct Upwind {
+    int k1, k2;
+    float w1, l1, l2;
+};
+
+// Upwind tables of a set of directions on one Voronoi grid.
+struct VorTables {
+    int ndir = 0;
+    std::vector<double> dirs;                  // [ndir][3]
+    std::vector<Upwind> h_up;                  // [ndir][nsites], site order
+    std::vector<int32_t> h_level;              // [ndir][nsites]
+    std::vector<std::vector<int64_t>> lvl_off; // per direction: level offsets into the slots
+    Upwind *d_up = nullptr;                    // [ndir][nsites], slot (level) order
+    int32_t *d_order = nullptr;                // [ndir][nsites]: site held by each slot
+    int max_levels = 0;
+    int64_t n_fallback = 0;
+    void release();
+};
+
+struct Scratch {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace rt
+
+struct rt_grid {
+    int kind;
+    int device;
+    int ndir;
+    std::vector<double> dirs, wdir;
+    int periodic;
+    int64_t npt;
+    // regular
+    int nx = 0, ny = 0, nz = 0;
+    double dx = 0, dy = 0;
+    std::vector<double> z;
+    std::vector<int> dir_up, dir_dn;           // direction indices per hemisphere
+    rt::Stencil *d_stencil = nullptr;          // [nz][ndir]; plane k's stencil to its upwind
+    std::vector<rt::Stencil> h_stencil;
+    rt::Stencil *d_stencil_one = nullptr;      // [nz]: one extra direction (emergent/adjoint)
+    std::vector<rt::Stencil> h_stencil_one;
+    double one_dir[3] = {0, 0, 0};
+    // voronoi
+    std::vector<double> xyz;
+    double box[6];
+    int64_t nsites = 0;
+    double r_exp = 7.0;
+    std::vector<int64_t> nbr_off;
+    std::vector<int32_t> nbr_idx;
+    std::vector<int8_t> nbr_shift;
+    rt::VorTables vt;                          // the quadrature directions
+    rt::VorTables vt_one;                      // cache: one extra direction (emergent/adjoint)
+    int64_t n_fallback = 0;
+    int max_levels = 0;
+    std::vector<int64_t> top;                  // emergent-layer points
+    int64_t *d_top = nullptr;
+    // shared
+    unsigned *d_err = nullptr;                 // device error word
+    rt::Scratch scratch[4];
+    ~rt_grid();
+};
+
+namespace rt {
+rt_status scratch_get(rt_grid *g, int slot, size_t bytes, void **out);
+rt_status check_dev_error(rt_grid *g, cudaStream_t st);
+
+// launchers (defined in the .cu files)
+rt_status regular_formal_solution(rt_grid *g, int nlam, const float *alpha, const float *S, int bc,
+                                  const float *I_bc, float *J, float *I_dir, cudaStream_t st);
+rt_status regular_emergent(rt_grid *g, const double *dir, int nlam, const float *alpha,
+                           const float *S, int bc, float *I_top, cudaStream_t st);
+size_t regular_adjoint_ws(rt_grid *g, int nlam, int stride);
+rt_status regular_adjoint(rt_grid *g, const double *dir, int nlam, const float *alpha,
+                          const float *S, int bc, const float *gI_top, float *g_alpha, float *g_S,
+                          int stride, void *ws, size_t ws_bytes, cudaStream_t st);
+rt_status voronoi_formal_solution(rt_grid *g, int nlam, const float *alpha, const float *S, int bc,
+                                  const float *I_bc, float *J, float *I_dir, cudaStream_t st);
+rt_status voronoi_emergent(rt_grid *g, const double *dir, int nlam, const float *alpha,
+                           const float *S, int bc, float *I_top, cudaStream_t st);
+size_t voronoi_adjoint_ws(rt_grid *g, int nlam, int stride);
+rt_status voronoi_adjoint(rt_grid *g, const double *dir, int nlam, const float *alpha,
+                          const float *S, int bc, const float *gI_top, float *g_alpha, float *g_S,
+                          int stride, void *ws, size_t ws_bytes, cudaStream_t st);
+// stencils of one direction for every plane (regular grid), host-built
+std::vector<Stencil> regular_dir_stencils(const rt_grid *g, const double *u);
+// upwind tables of the given directions (Voronoi), built on the host and uploaded
+rt_status voronoi_build_tables(const rt_grid *g, int ndir, const double *dirs, VorTables &vt,
+                               cudaStream_t st);
+// tables of one extra direction, cached on the grid
+rt_status voronoi_dir_tables_cached(rt_grid *g, const double *dir, VorTables **out,
+                                    cudaStream_t st);
+}  // namespace rt

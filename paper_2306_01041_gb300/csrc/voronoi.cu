@@ -1,0 +1,398 @@
+// Voronoi grid: transport along Delaunay lines from the two best-aligned upwind neighbours
+// (Sect. 2.5, Eq. 5 and the weight formula after it) with linear S across each segment (Eq. 2),
+// swept per direction in dependency levels; J = sum_d w_d I_d (Eq. 4) in a fixed direction order.
+//
+// Layout: the fields are transposed once per call to site-major [nsites][nlam] so that the
+// gather of an upwind site reads one contiguous wavelength vector; a thread owns one
+// (site, wavelength) of the current level.
+#include <algorithm>
+#include <cmath>
+
+#include "device_common.cuh"
+#include "rt_impl.h"
+
+namespace rt {
+
+// [rows][cols] -> [cols][rows]
+__global__ void transpose_kernel(const float *__restrict__ in, float *__restrict__ out, int rows,
+                                 int cols)
+{
+    __shared__ float tile[32][33];
+    int c = blockIdx.x * 32 + threadIdx.x;
+    int r0 = blockIdx.y * 32;
+    for (int dr = threadIdx.y; dr < 32; dr += blockDim.y) {
+        int r = r0 + dr;
+        if (r < rows && c < cols) tile[dr][threadIdx.x] = in[(size_t)r * cols + c];
+    }
+    __syncthreads();
+    int r = r0 + threadIdx.x;
+    for (int dc = threadIdx.y; dc < 32; dc += blockDim.y) {
+        int cc = blockIdx.x * 32 + dc;
+        if (r < rows && cc < cols) out[(size_t)cc * rows + r] = tile[threadIdx.x][dc];
+    }
+}
+
+static void transpose(const float *in, float *out, int rows, int cols, cudaStream_t st)
+{
+    dim3 grid((cols + 31) / 32, (rows + 31) / 32);
+    transpose_kernel<<<grid, dim3(32, 8), 0, st>>>(in, out, rows, cols);
+}
+
+struct VorArgs {
+    const Upwind *up;        // slot-ordered records of this direction
+    const int32_t *order;    // slot -> site
+    const float *A, *S;      // [n][nlam]
+    float *I;                // [n][nlam] this direction
+    float *J;                // [n][nlam] or null
+    const float *I_bc;       // [nlam][n] of this direction (RT_BC_ARRAY) or null
+    unsigned *err;
+    int64_t s0, s1;          // slot range of the level
+    int nlam, n, up_dir, bc, first;
+    float w;
+};
+
+// Intensity of one site for one wavelength (Eq. 5 with linear S on each segment).
+__device__ __forceinline__ float site_intensity(const Upwind &u, int i, int l, const VorArgs &a)
+{
+    const size_t il = (size_t)i * a.nlam + l;
+    const float Si = __ldg(a.S + il), Ai = __ldg(a.A + il);
+    float acc = 0.f;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const int k = c ? u.k2 : u.k1;
+        const float wk = c ? 1.f - u.w1 : u.w1;
+        const float len = c ? u.l2 : u.l1;
+        if (wk == 0.f) continue;
+        float Ik, Sk, Ak;
+        if (k >= 0) {
+            const size_t kl = (size_t)k * a.nlam + l;
+            Ik = a.I[kl];
+            Sk = __ldg(a.S + kl);
+            Ak = __ldg(a.A + kl);
+        } else {
+            Sk = Si;
+            Ak = Ai;
+            if (a.bc == RT_BC_ARRAY) Ik = __ldg(a.I_bc + (size_t)l * a.n + i);
+            else Ik = (a.bc == RT_BC_THERMAL && a.up_dir && k == -1) ? Si : 0.f;
+        }
+        float ex, w0, w1;
+        lin_weights(0.5f * (Ak + Ai) * len, ex, w0, w1);
+        acc += wk * (Ik * ex + w0 * Sk + w1 * Si);
+    }
+    return acc;
+}
+
+__global__ void __launch_bounds__(256) vor_level_kernel(const VorArgs a)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t slot = a.s0 + t / a.nlam;
+    const int l = (int)(t % a.nlam);
+    if (slot >= a.s1) return;
+    const Upwind u = a.up[slot];
+    const int i = a.order[slot];
+    const float v = site_intensity(u, i, l, a);
+    const size_t il = (size_t)i * a.nlam + l;
+    a.I[il] = v;
+    if (a.J) {
+        const float jv = a.first ? a.w * v : a.J[il] + a.w * v;
+        if (!isfinite(jv)) flag_error(a.err, ERR_NAN);
+        a.J[il] = jv;
+    }
+}
+
+static void sweep_direction(const rt_grid *g, const VorTables &vt, int d, VorArgs &a,
+                            cudaStream_t st)
+{
+    const int64_t n = g->nsites;
+    a.up = vt.d_up + (size_t)d * n;
+    a.order = vt.d_order + (size_t)d * n;
+    a.up_dir = vt.dirs[3 * d + 2] > 0;
+    const std::vector<int64_t> &off = vt.lvl_off[d];
+    for (size_t L = 0; L + 1 < off.size(); ++L) {
+        a.s0 = off[L];
+        a.s1 = off[L + 1];
+        const int64_t work = (a.s1 - a.s0) * a.nlam;
+        if (work <= 0) continue;
+        vor_level_kernel<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(a);
+    }
+}
+
+rt_status voronoi_formal_solution(rt_grid *g, int nlam, const float *alpha, const float *S,
+                                  int bc, const float *I_bc, float *J, float *I_dir,
+                                  cudaStream_t st)
+{
+    const int64_t n = g->nsites;
+    const size_t f = (size_t)n * nlam;
+    void *p;
+    RT_TRY(scratch_get(g, 0, 4 * f * sizeof(float) + (bc == RT_BC_ARRAY ? 0 : 0), &p));
+    float *At = (float *)p, *St = At + f, *It = St + f, *Jt = It + f;
+    transpose(alpha, At, nlam, (int)n, st);
+    transpose(S, St, nlam, (int)n, st);
+    VorArgs a;
+    a.A = At;
+    a.S = St;
+    a.I = It;
+    a.J = Jt;
+    a.err = g->d_err;
+    a.nlam = nlam;
+    a.n = (int)n;
+    a.bc = bc;
+    for (int d = 0; d < g->ndir; ++d) {
+        a.first = d == 0;
+        a.w = (float)g->wdir[d];
+        a.I_bc = bc == RT_BC_ARRAY ? I_bc + (size_t)d * f : nullptr;
+        sweep_direction(g, g->vt, d, a, st);
+        if (I_dir) transpose(It, I_dir + (size_t)d * f, (int)n, nlam, st);
+    }
+    transpose(Jt, J, (int)n, nlam, st);
+    RT_CUDA(cudaGetLastError());
+    return RT_OK;
+}
+
+__global__ void gather_top_kernel(const float *I, const int64_t *top, float *out, int64_t ntop,
+                                  int nlam)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntop * nlam) return;
+    const int l = (int)(t / ntop);
+    const int64_t s = t % ntop;
+    out[t] = I[(size_t)top[s] * nlam + l];
+}
+
+// forward sweep of one direction into It [n][nlam] (At, St already transposed)
+static rt_status one_dir_forward(rt_grid *g, const VorTables &vt, int nlam, const float *At,
+                                 const float *St, float *It, int bc, cudaStream_t st)
+{
+    VorArgs a;
+    a.A = At;
+    a.S = St;
+    a.I = It;
+    a.J = nullptr;
+    a.I_bc = nullptr;
+    a.err = g->d_err;
+    a.nlam = nlam;
+    a.n = (int)g->nsites;
+    a.bc = bc;
+    a.first = 1;
+    a.w = 1.f;
+    sweep_direction(g, vt, 0, a, st);
+    RT_CUDA(cudaGetLastError());
+    return RT_OK;
+}
+
+rt_status voronoi_emergent(rt_grid *g, const double *dir, int nlam, const float *alpha,
+                           const float *S, int bc, float *I_top, cudaStream_t st)
+{
+    VorTables *vt;
+    RT_TRY(voronoi_dir_tables_cached(g, dir, &vt, st));
+    const int64_t n = g->nsites;
+    const size_t f = (size_t)n * nlam;
+    void *p;
+    RT_TRY(scratch_get(g, 1, 3 * f * sizeof(float), &p));
+    float *At = (float *)p, *St = At + f, *It = St + f;
+    transpose(alpha, At, nlam, (int)n, st);
+    transpose(S, St, nlam, (int)n, st);
+    RT_TRY(one_dir_forward(g, *vt, nlam, At, St, It, bc, st));
+    const int64_t ntop = (int64_t)g->top.size();
+    if (ntop)
+        gather_top_kernel<<<(unsigned)((ntop * nlam + 255) / 256), 256, 0, st>>>(It, g->d_top,
+                                                                                 I_top, ntop, nlam);
+    RT_CUDA(cudaGetLastError());
+    return RT_OK;
+}
+
+// ---- adjoint ---------------------------------------------------------------------------------
+// Reverse level order with a downwind list per site (the transpose of the upwind links), so
+// every adjoint value is a gather: for site k with downwind pairs (i, c) (k is the c-th upwind of
+// i), dL/dI_k = gI_loss(k) + sum w_c(i) e_c(i) dL/dI_i and the S, alpha gradients collect the
+// matching w0 and dtau terms; then k adds the terms of its own segments (w1 S_k and alpha_k).
+struct AdjV {
+    const Upwind *up_site;   // [n] records in site order
+    const int32_t *order;    // level-ordered sites
+    const int64_t *doff;     // [n+1] downwind CSR
+    const int32_t *dsite;    // downwind site
+    const int8_t *dcomp;     // which upwind slot (0, 1) of that site
+    const float *A, *S, *I;  // [n][nlam]
+    float *G;                // [n][nlam] dL/dI (seeded with the loss gradient)
+    float *gA, *gS;          // [n][nlam]
+    int64_t s0, s1;
+    int nlam, up_dir, bc;
+};
+
+__global__ void __launch_bounds__(256) vor_adj_level(const AdjV a)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t slot = a.s0 + t / a.nlam;
+    const int l = (int)(t % a.nlam);
+    if (slot >= a.s1) return;
+    const int k = a.order[slot];
+    const size_t kl = (size_t)k * a.nlam + l;
+    const float Sk = __ldg(a.S + kl), Ak = __ldg(a.A + kl), Ik = a.I[kl];
+    float g = a.G[kl], gs = 0.f, ga = 0.f;
+    // contributions of the downwind sites (all at higher levels, already final)
+    for (int64_t e = a.doff[k]; e < a.doff[k + 1]; ++e) {
+        const int i = a.dsite[e];
+        const int c = a.dcomp[e];
+        const Upwind u = a.up_site[i];
+        const float wk = c ? 1.f - u.w1 : u.w1;
+        const float len = c ? u.l2 : u.l1;
+        const size_t il = (size_t)i * a.nlam + l;
+        const float Si = __ldg(a.S + il), Ai = __ldg(a.A + il), gi = a.G[il] * wk;
+        const float dt = 0.5f * (Ak + Ai) * len;
+        float ex, w0, w1, dex, dw0, dw1;
+        lin_weights(dt, ex, w0, w1);
+        lin_weights_deriv(dt, ex, dex, dw0, dw1);
+        const float gd = gi * (Ik * dex + Sk * dw0 + Si * dw1);
+        g += ex * gi;
+        gs += w0 * gi;
+        ga += 0.5f * len * gd;
+    }
+    a.G[kl] = g;
+    // k's own segments
+    const Upwind u = a.up_site[k];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const int m = c ? u.k2 : u.k1;
+        const float wk = c ? 1.f - u.w1 : u.w1;
+        const float len = c ? u.l2 : u.l1;
+        if (wk == 0.f) continue;
+        float Im, Sm, Am;
+        const bool wall = m < 0;
+        const bool thermal = wall && a.bc == RT_BC_THERMAL && a.up_dir && m == -1;
+        if (!wall) {
+            const size_t ml = (size_t)m * a.nlam + l;
+            Im = a.I[ml];
+            Sm = __ldg(a.S + ml);
+            Am = __ldg(a.A + ml);
+        } else {
+            Sm = Sk;
+            Am = Ak;
+            Im = thermal ? Sk : 0.f;
+        }
+        const float dt = 0.5f * (Am + Ak) * len;
+        float ex, w0, w1, dex, dw0, dw1;
+        lin_weights(dt, ex, w0, w1);
+        lin_weights_deriv(dt, ex, dex, dw0, dw1);
+        const float gk = wk * g;
+        const float gd = gk * (Im * dex + Sm * dw0 + Sk * dw1);
+        gs += w1 * gk;
+        ga += 0.5f * len * gd;
+        if (wall) {   // the wall node carries the site's own S and alpha (and I = S if thermal)
+            gs += w0 * gk + (thermal ? ex * gk : 0.f);
+            ga += 0.5f * len * gd;
+        }
+    }
+    a.gS[kl] = gs;
+    a.gA[kl] = ga;
+}
+
+__global__ void scatter_top_kernel(const float *gI_top, const int64_t *top, float *G,
+                                   int64_t ntop, int nlam)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntop * nlam) return;
+    const int l = (int)(t / ntop);
+    const int64_t s = t % ntop;
+    G[(size_t)top[s] * nlam + l] = gI_top[t];
+}
+
+// workspace: At, St, It, G, gAt, gSt [n][nlam] + up_site [n] + downwind CSR (n+1 + 2n + 2n)
+size_t voronoi_adjoint_ws(rt_grid *g, int nlam, int stride)
+{
+    (void)stride;
+    const size_t n = (size_t)g->nsites;
+    return 6 * n * nlam * sizeof(float) + n * sizeof(Upwind) + (n + 1) * sizeof(int64_t) +
+           2 * n * sizeof(int32_t) + 2 * n * sizeof(int8_t) + 64 * 5;
+}
+
+static inline char *align_up(char *p)
+{
+    return (char *)(((uintptr_t)p + 63) & ~(uintptr_t)63);
+}
+
+rt_status voronoi_adjoint(rt_grid *g, const double *dir, int nlam, const float *alpha,
+                          const float *S, int bc, const float *gI_top, float *g_alpha, float *g_S,
+                          int stride, void *ws, size_t ws_bytes, cudaStream_t st)
+{
+    (void)stride;
+    (void)ws_bytes;
+    VorTables *vt;
+    RT_TRY(voronoi_dir_tables_cached(g, dir, &vt, st));
+    const int64_t n = g->nsites;
+    const size_t f = (size_t)n * nlam;
+    // downwind CSR of this direction (host)
+    std::vector<int64_t> doff(n + 1, 0);
+    for (int64_t i = 0; i < n; ++i) {
+        const Upwind &u = vt->h_up[i];
+        if (u.k1 >= 0) doff[u.k1 + 1]++;
+        if (u.w1 < 1.f && u.k2 >= 0) doff[u.k2 + 1]++;
+    }
+    for (int64_t i = 0; i < n; ++i) doff[i + 1] += doff[i];
+    std::vector<int32_t> dsite(doff[n]);
+    std::vector<int8_t> dcomp(doff[n]);
+    std::vector<int64_t> pos(doff.begin(), doff.end() - 1);
+    for (int64_t i = 0; i < n; ++i) {
+        const Upwind &u = vt->h_up[i];
+        if (u.k1 >= 0) { dsite[pos[u.k1]] = (int32_t)i; dcomp[pos[u.k1]++] = 0; }
+        if (u.w1 < 1.f && u.k2 >= 0) { dsite[pos[u.k2]] = (int32_t)i; dcomp[pos[u.k2]++] = 1; }
+    }
+    char *c = align_up((char *)ws);
+    float *At = (float *)c, *St = At + f, *It = St + f, *G = It + f, *gAt = G + f, *gSt = gAt + f;
+    c = align_up((char *)(gSt + f));
+    Upwind *d_up_site = (Upwind *)c;
+    c = align_up((char *)(d_up_site + n));
+    int64_t *d_doff = (int64_t *)c;
+    c = align_up((char *)(d_doff + n + 1));
+    int32_t *d_dsite = (int32_t *)c;
+    c = align_up((char *)(d_dsite + std::max<int64_t>(doff[n], 1)));
+    int8_t *d_dcomp = (int8_t *)c;
+    RT_CUDA(cudaMemcpyAsync(d_up_site, vt->h_up.data(), n * sizeof(Upwind), cudaMemcpyHostToDevice,
+                            st));
+    RT_CUDA(cudaMemcpyAsync(d_doff, doff.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice,
+                            st));
+    if (doff[n]) {
+        RT_CUDA(cudaMemcpyAsync(d_dsite, dsite.data(), doff[n] * sizeof(int32_t),
+                                cudaMemcpyHostToDevice, st));
+        RT_CUDA(cudaMemcpyAsync(d_dcomp, dcomp.data(), doff[n] * sizeof(int8_t),
+                                cudaMemcpyHostToDevice, st));
+    }
+    transpose(alpha, At, nlam, (int)n, st);
+    transpose(S, St, nlam, (int)n, st);
+    RT_TRY(one_dir_forward(g, *vt, nlam, At, St, It, bc, st));
+    RT_CUDA(cudaMemsetAsync(G, 0, f * sizeof(float), st));
+    const int64_t ntop = (int64_t)g->top.size();
+    if (ntop)
+        scatter_top_kernel<<<(unsigned)((ntop * nlam + 255) / 256), 256, 0, st>>>(gI_top, g->d_top,
+                                                                                  G, ntop, nlam);
+    AdjV a;
+    a.up_site = d_up_site;
+    a.order = vt->d_order;
+    a.doff = d_doff;
+    a.dsite = d_dsite;
+    a.dcomp = d_dcomp;
+    a.A = At;
+    a.S = St;
+    a.I = It;
+    a.G = G;
+    a.gA = gAt;
+    a.gS = gSt;
+    a.nlam = nlam;
+    a.up_dir = 1;
+    a.bc = bc;
+    const std::vector<int64_t> &off = vt->lvl_off[0];
+    for (int L = (int)off.size() - 2; L >= 0; --L) {
+        a.s0 = off[L];
+        a.s1 = off[L + 1];
+        const int64_t work = (a.s1 - a.s0) * nlam;
+        if (work <= 0) continue;
+        vor_adj_level<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(a);
+    }
+    transpose(gAt, g_alpha, (int)n, nlam, st);
+    transpose(gSt, g_S, (int)n, nlam, st);
+    RT_CUDA(cudaGetLastError());
+    // the host vectors above were copied with pageable cudaMemcpyAsync, which completes before
+    // returning; nothing on the host outlives this call
+    return RT_OK;
+}
+
+}  // namespace rt
