@@ -33,7 +33,7 @@ WORKLOAD = "NLTE Lambda iteration, regular grid 128x128x128, 52 wavelengths, 24 
 
 # DRAM bytes per launch of the dominant kernel from the ncu capture summarised in profiles/,
 # valid only for the kernel source with this hash (else reported as null)
-PROFILED = {"file": "paper_2306_01041_gb300/csrc/regular.cu", "sha1": None,
+PROFILED = {"file": "paper_2306_01041_gb300/csrc/regular_tile.cu", "sha1": None,
             "dram_bytes_per_launch": None}
 
 # FP32 FLOPs per point-direction-wavelength update of the sweep: three bilinear interpolations
@@ -144,21 +144,39 @@ def run_gpu(args):
     S = torch.empty_like(alpha)
     J = torch.empty_like(alpha)
 
-    ev_fs = []
+    # One Lambda iteration = source terms -> formal solution (+ J) -> statistical equilibrium ->
+    # read-back of max |dn/n|.  The device part is captured once as a CUDA graph and replayed.
+    dmax_host = torch.zeros(1, dtype=torch.float32).pin_memory()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
 
-    def step(record=False):
-        a, s = rt.source_terms(g, atom, atmos, pops)
+    def body(st):
+        a, s = rt.source_terms(g, atom, atmos, pops, stream=st)
         alpha.copy_(a)
         S.copy_(s)
+        ev[0].record(st)
+        rt.formal_solution(g, alpha, S, J=J, stream=st)
+        ev[1].record(st)
+        d = rt.statistical_equilibrium(g, atom, atmos, J, pops, stream=st)
+        dmax_host.copy_(d, non_blocking=True)
+
+    cap = torch.cuda.Stream(device=dev)
+    cap.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(cap):
+        body(cap)                      # allocates the library's scratch before capture
+        cap.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=cap):
+            body(cap)
+    torch.cuda.current_stream().wait_stream(cap)
+    stream = torch.cuda.current_stream()
+    fs_times = []
+
+    def step(record=False):
+        graph.replay()
+        torch.cuda.current_stream().synchronize()   # the convergence read-back
         if record:
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-        rt.formal_solution(g, alpha, S, J=J)
-        if record:
-            e1.record(stream)
-            ev_fs.append((e0, e1))
-        d = rt.statistical_equilibrium(g, atom, atmos, J, pops)
-        return float(d.item())          # the convergence read-back (one scalar D2H)
+            fs_times.append(ev[0].elapsed_time(ev[1]))
+        return float(dmax_host.item())
 
     for _ in range(args.warmup):
         step()
@@ -184,8 +202,8 @@ def run_gpu(args):
         ms = float(tt.item())
     updates = npt * NDIR * nlam
     value = updates * world / (ms * 1e-3) / 1e9
-    fs_ms = statistics.mean(a.elapsed_time(b) for a, b in ev_fs)
-    launches_fs = 2 * NZ
+    fs_ms = statistics.mean(fs_times)
+    launches_fs = 2 * (NZ - 1)
     per_launch_ms = fs_ms / launches_fs
     flops_launch = FLOP_PER_UPDATE * NX * NY * (NDIR // 2) * nlam
     achieved = flops_launch / (per_launch_ms * 1e-3) / 1e12
@@ -228,8 +246,8 @@ def run_gpu(args):
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": round(updates / (e_ms * 1e-3) / 1e9, 3), "unit": "Gupd/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": args.steps * (1 + launches_fs + 1),
-        "roofline": {"bound": "alu", "kernel": "sc_plane_kernel",
+        "gpu_launches": args.steps * (1 + 2 * NZ + 1),
+        "roofline": {"bound": "alu", "kernel": "sc_tile_kernel",
                      "achieved": round(achieved, 3), "peak": round(ALU_PEAK_TFLOPS, 2),
                      "unit": "TFLOP/s", "frac": round(achieved / ALU_PEAK_TFLOPS, 4),
                      "traffic": traffic,
@@ -468,8 +486,14 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-lams", type=int, default=2)
+    ap.add_argument("--cpu-lams", type=int, default=52)
+    ap.add_argument("--nx", type=int, default=128,
+                    help="grid size per axis (profiling uses smaller cases; the benchmark is 128)")
     args = ap.parse_args()
+    global NX, NY, NZ, WORKLOAD
+    if args.nx != 128:
+        NX = NY = NZ = args.nx
+        WORKLOAD = WORKLOAD.replace("128x128x128", f"{NX}x{NY}x{NZ}")
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -21,6 +21,7 @@ rt_status fail(rt_status st, const std::string &msg)
 rt_status cuda_fail(cudaError_t e, const char *what)
 {
     g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    cudaGetLastError();   // clear a non-sticky error so that it does not resurface later
     return e == cudaErrorMemoryAllocation ? RT_ENOMEM : RT_ECUDA;
 }
 
@@ -83,6 +84,30 @@ std::vector<Stencil> regular_dir_stencils(const rt_grid *g, const double *u)
         int ku = u[2] > 0 ? k - 1 : k + 1;
         if (ku < 0 || ku >= g->nz) continue;
         out[k] = plane_stencil(g->z[k] - g->z[ku], u, g->dx, g->dy, g->nx, g->ny);
+    }
+    return out;
+}
+
+std::vector<StencilD> regular_dir_stencils_d(const rt_grid *g, const double *u)
+{
+    std::vector<StencilD> out((size_t)g->nz, StencilD{});
+    for (int k = 0; k < g->nz; ++k) {
+        int ku = u[2] > 0 ? k - 1 : k + 1;
+        if (ku < 0 || ku >= g->nz) continue;
+        const double ds = std::fabs(g->z[k] - g->z[ku]) / std::fabs(u[2]);
+        const double cx = -ds * u[0] / g->dx, cy = -ds * u[1] / g->dy;
+        const double fx = std::floor(cx), fy = std::floor(cy);
+        const double tx = cx - fx, ty = cy - fy;
+        StencilD &s = out[k];
+        s.ax = (int)fx;
+        s.ay = (int)fy;
+        s.axm = ((s.ax % g->nx) + g->nx) % g->nx;
+        s.aym = ((s.ay % g->ny) + g->ny) % g->ny;
+        s.w0 = (1.0 - tx) * (1.0 - ty);
+        s.w1 = tx * (1.0 - ty);
+        s.w2 = (1.0 - tx) * ty;
+        s.w3 = tx * ty;
+        s.hds = 0.5 * ds;
     }
     return out;
 }
@@ -156,7 +181,8 @@ static inline NbrGeom neighbour(const rt_grid *g, int32_t code, int8_t shift)
 // crossing to the site.  With no competitor the most nearly vertical upwind neighbour is used.
 static void voronoi_dir_tables(const rt_grid *g, const int64_t *off, const int32_t *code,
                                const int8_t *shift, const double *u, double r,
-                               std::vector<Upwind> &out, int64_t &nfb)
+                               std::vector<Upwind> &out, int64_t &nfb,
+                               std::vector<UpwindD> *outd = nullptr)
 {
     const int64_t n = g->nsites;
     const double sgn = u[2] > 0 ? 1.0 : -1.0;
@@ -203,12 +229,15 @@ static void voronoi_dir_tables(const rt_grid *g, const int64_t *off, const int32
             ++nc;
         }
         Upwind w;
+        UpwindD wd;
         if (nc >= 2) {
             double a = std::pow(best[0].v, r), b = std::pow(best[1].v, r);
             w = Upwind{best[0].k, best[1].k, (float)(a / (a + b)), (float)best[0].len,
                        (float)best[1].len};
+            wd = UpwindD{best[0].k, best[1].k, a / (a + b), b / (a + b), best[0].len, best[1].len};
         } else if (nc == 1) {
             w = Upwind{best[0].k, best[0].k, 1.0f, (float)best[0].len, (float)best[0].len};
+            wd = UpwindD{best[0].k, best[0].k, 1.0, 0.0, best[0].len, best[0].len};
         } else {
             ++fb;
             if (vert_best < 0.0) {
@@ -216,8 +245,10 @@ static void voronoi_dir_tables(const rt_grid *g, const int64_t *off, const int32
                 vert_len = (u[2] > 0 ? xi[2] - g->box[4] : g->box[5] - xi[2]) / std::fabs(u[2]);
             }
             w = Upwind{vert_k, vert_k, 1.0f, (float)vert_len, (float)vert_len};
+            wd = UpwindD{vert_k, vert_k, 1.0, 0.0, vert_len, vert_len};
         }
         out[i] = w;
+        if (outd) (*outd)[i] = wd;
     }
     nfb += fb;
 }
@@ -273,10 +304,12 @@ rt_status voronoi_build_tables(const rt_grid *g, int nd, const double *dirs, Vor
     vt.h_level.assign((size_t)nd * n, 0);
     vt.n_fallback = 0;
     const int8_t *sh = g->nbr_shift.empty() ? nullptr : g->nbr_shift.data();
+    if (nd == 1) vt.h_upd.assign(n, UpwindD{});
+    else vt.h_upd.clear();
     for (int q = 0; q < nd; ++q) {
         std::vector<Upwind> tmp(n);
         voronoi_dir_tables(g, g->nbr_off.data(), g->nbr_idx.data(), sh, &vt.dirs[3 * q],
-                           g->r_exp, tmp, vt.n_fallback);
+                           g->r_exp, tmp, vt.n_fallback, nd == 1 ? &vt.h_upd : nullptr);
         std::copy(tmp.begin(), tmp.end(), vt.h_up.begin() + (size_t)q * n);
         if (!voronoi_levels(g, &vt.dirs[3 * q], &vt.h_up[(size_t)q * n],
                             &vt.h_level[(size_t)q * n]))
@@ -386,6 +419,7 @@ rt_grid::~rt_grid()
 {
     if (d_stencil) cudaFree(d_stencil);
     if (d_stencil_one) cudaFree(d_stencil_one);
+    if (d_stencil_oned) cudaFree(d_stencil_oned);
     vt.release();
     vt_one.release();
     if (d_top) cudaFree(d_top);

@@ -26,6 +26,34 @@ __device__ __forceinline__ void lin_weights(float d, float &ex, float &w0, float
     }
 }
 
+// FP64 variant (used by the adjoint sweeps): series below d = 1e-3, truncation < 1e-19.
+__device__ __forceinline__ void lin_weights(double d, double &ex, double &w0, double &w1)
+{
+    ex = exp(-d);
+    if (d < 1e-3) {
+        w1 = d * (0.5 + d * (-1.0 / 6.0 + d * (1.0 / 24.0 + d * (-1.0 / 120.0 + d * (1.0 / 720.0)))));
+        w0 = d * (0.5 + d * (-1.0 / 3.0 + d * (1.0 / 8.0 + d * (-1.0 / 30.0 + d * (1.0 / 144.0)))));
+    } else {
+        const double e0 = -expm1(-d);
+        w1 = (d - e0) / d;
+        w0 = e0 - w1;
+    }
+}
+
+__device__ __forceinline__ void lin_weights_deriv(double d, double ex, double &dex, double &dw0,
+                                                  double &dw1)
+{
+    dex = -ex;
+    if (d < 1e-3) {
+        dw1 = 0.5 + d * (-1.0 / 3.0 + d * (1.0 / 8.0 + d * (-1.0 / 30.0 + d * (1.0 / 144.0))));
+        dw0 = 0.5 + d * (-2.0 / 3.0 + d * (3.0 / 8.0 + d * (-2.0 / 15.0 + d * (5.0 / 144.0))));
+    } else {
+        const double e0 = -expm1(-d);
+        dw1 = (e0 - d * ex) / (d * d);
+        dw0 = ex - dw1;
+    }
+}
+
 // d/dd of (e^-d, w0, w1), for the adjoint sweeps.
 __device__ __forceinline__ void lin_weights_deriv(float d, float ex, float &dex, float &dw0,
                                                   float &dw1)

@@ -43,6 +43,7 @@ struct AtomDev {
     float inv_k;                      // 1/k
     // per wavelength
     float lam[MAX_LAM];
+    float dlam[MAX_LAM];              // lambda - lambda0 (taken in double: FP32 would cancel)
     int kind[MAX_LAM];
     float wline[MAX_LAM];             // line quadrature weight (profile normalisation)
     float sig_bf[2][MAX_LAM];         // bound-free cross sections (0 above the edge)
@@ -185,7 +186,7 @@ __device__ inline void source_node(int j, R T, R rho, float ne, const float *pop
     const R B = planck_dev<R>(j, T);
     R al = abg, eta = abg * B;
     if (A.kind[j] == 0) {
-        const R v = R(A.lam[j] - A.lam0) / dld;
+        const R v = R(A.dlam[j]) / dld;
         const R phi = voigt_H<R>(A.a, v) * R(0.56418958354775628f) / dld * phi_norm_inv;
         const R sig = R(A.c_line) * phi;
         const R g = R(A.g1_g2) * dexp(R(A.dE_line[j]) / kT);
@@ -211,7 +212,7 @@ template <class R> __device__ inline R phi_norm_inv(R dld)
     R s = R(0.f);
     for (int j = 0; j < c_atom.nlam; ++j) {
         if (c_atom.kind[j] != 0) continue;
-        const R v = R(c_atom.lam[j] - c_atom.lam0) / dld;
+        const R v = R(c_atom.dlam[j]) / dld;
         s = s + R(c_atom.wline[j]) * voigt_H<R>(c_atom.a, v) * R(0.56418958354775628f) / dld;
     }
     return R(1.f) / s;
@@ -300,7 +301,7 @@ __global__ void __launch_bounds__(256) se_kernel(int64_t npt, const float *T, co
             float sig, g;
             int lo, hi;
             if (A.kind[j] == 0) {
-                const float v = (A.lam[j] - A.lam0) / dld;
+                const float v = A.dlam[j] / dld;
                 sig = A.c_line * voigt_H<float>(A.a, v) * 0.56418958354775628f / dld * ninv;
                 g = A.g1_g2 * expf(A.dE_line[j] / kT);
                 lo = 0;
@@ -323,8 +324,9 @@ __global__ void __launch_bounds__(256) se_kernel(int64_t npt, const float *T, co
         for (int i = 0; i < 2; ++i) {
             const float cip = cb * expf(-A.chi[i] / kT);
             P[i][2] += cip;
-            // C_pi = C_ip n_e Phi_i = cb n_e g_i/(2 g_p) saha_c T^-1.5 (exponentials cancel)
-            P[2][i] += cb * e * A.saha_g[i] * A.saha_c * tm32;
+            // C_pi = C_ip n_e Phi_i = cb n_e g_i/(2 g_p) saha_c T^-1.5 (exponentials cancel);
+            // n_e saha_c is formed first: cb n_e alone can exceed the FP32 range
+            P[2][i] += cb * ((e * A.saha_c) * tm32 * A.saha_g[i]);
         }
         // scale to avoid FP32 range issues in the products
         float m = 0.f;
@@ -442,6 +444,7 @@ static rt_status load_atom(const rt_atom *at)
         const double l = at->lam[j];
         if (!(l > 0) || at->kind[j] < 0 || at->kind[j] > 2) return fail(RT_EINVAL, "bad wavelength node");
         A.lam[j] = (float)l;
+        A.dlam[j] = (float)(l - lam0);
         A.kind[j] = at->kind[j];
         A.wline[j] = at->kind[j] == 0 ? (float)at->wlam[j] : 0.f;
         nline += at->kind[j] == 0;
@@ -596,6 +599,17 @@ rt_status rt_lambda_iterate(rt_grid_t g, const rt_atom *atom, const rt_atmos *at
         RT_CUDA(cudaMemcpyAsync(h_dmax, dmax, sizeof(float), cudaMemcpyDeviceToHost, st));
         return RT_OK;
     };
+    cudaStream_t cs = nullptr;       // capture stream (the legacy default stream cannot be captured)
+    cudaEvent_t ev = nullptr;
+    struct StreamGuard {
+        cudaStream_t *s;
+        cudaEvent_t *e;
+        ~StreamGuard()
+        {
+            if (*e) cudaEventDestroy(*e);
+            if (*s) cudaStreamDestroy(*s);
+        }
+    } sguard{&cs, &ev};
     if (use_graph) {
         // the formal solution allocates its scratch on first use: do that before capturing
         void *q;
@@ -604,10 +618,18 @@ rt_status rt_lambda_iterate(rt_grid_t g, const rt_atom *atom, const rt_atmos *at
             RT_TRY(scratch_get(g, 0, 2 * (size_t)nlam * ndh * g->nx * g->ny * sizeof(float), &q));
         else
             RT_TRY(scratch_get(g, 0, 4 * (size_t)n * nlam * sizeof(float), &q));
-        RT_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        RT_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        RT_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        RT_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        cudaStream_t user = st;
+        st = cs;
         rt_status s = enqueue();
-        cudaError_t e = cudaStreamEndCapture(st, &guard.gr);
-        if (s != RT_OK) return s;
+        st = user;
+        cudaError_t e = cudaStreamEndCapture(cs, &guard.gr);
+        if (s != RT_OK) {
+            cudaGetLastError();
+            return s;
+        }
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
         RT_CUDA(cudaGraphInstantiate(&guard.ex, guard.gr, 0));
     }

@@ -14,14 +14,14 @@
 
 namespace rt {
 
-struct SweepArgs {
+template <class T, class ST = Stencil> struct SweepArgsT {
     const float *alpha, *S;      // [nlam][npt]
-    const float *Iprev;          // [nlam][ndh][np]
-    float *Inext;                // [nlam][ndh][np]
+    const T *Iprev;              // [nlam][ndh][np]
+    T *Inext;                    // [nlam][ndh][np]
     float *J;                    // [nlam][npt] or null
     float *I_dir;                // [ndir][nlam][npt] or null
     const float *I_bc;           // [ndir][nlam][np] or null
-    const Stencil *st;           // [nz][st_stride]
+    const ST *st;                // [nz][st_stride]
     unsigned *err;
     int nx, ny, nz, np, nlam, ndh, ndir, st_stride;
     int up, periodic, bc, first;
@@ -29,15 +29,27 @@ struct SweepArgs {
     int dst[MAX_DIR];            // stencil column of each hemisphere slot
     float w[MAX_DIR];            // quadrature weight of each slot
 };
+using SweepArgs = SweepArgsT<float>;
 
-__device__ __forceinline__ float bilerp(const float *__restrict__ P, int o00, int o10, int o01,
-                                        int o11, const Stencil &s)
+template <class T, class ST>
+__device__ __forceinline__ T bilerp(const T *__restrict__ P, int o00, int o10, int o01, int o11,
+                                    const ST &s)
 {
-    return s.w0 * __ldg(P + o00) + s.w1 * __ldg(P + o10) + s.w2 * __ldg(P + o01) +
-           s.w3 * __ldg(P + o11);
+    return (T)s.w0 * __ldg(P + o00) + (T)s.w1 * __ldg(P + o10) + (T)s.w2 * __ldg(P + o01) +
+           (T)s.w3 * __ldg(P + o11);
 }
 
-__global__ void __launch_bounds__(256) sc_plane_kernel(const SweepArgs a, int step)
+template <class T, class ST>
+__device__ __forceinline__ T bilerp_f(const float *__restrict__ P, int o00, int o10, int o01,
+                                      int o11, const ST &s)
+{
+    return (T)s.w0 * (T)__ldg(P + o00) + (T)s.w1 * (T)__ldg(P + o10) +
+           (T)s.w2 * (T)__ldg(P + o01) + (T)s.w3 * (T)__ldg(P + o11);
+}
+
+// T = float for the formal solution; T = double for the adjoint's forward recomputation
+template <class T, class ST = Stencil>
+__global__ void __launch_bounds__(256) sc_plane_kernel(const SweepArgsT<T, ST> a, int step)
 {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     const int l = blockIdx.y;
@@ -47,28 +59,29 @@ __global__ void __launch_bounds__(256) sc_plane_kernel(const SweepArgs a, int st
     const size_t npt = (size_t)a.np * a.nz;
     const float *al = a.alpha + (size_t)l * npt;
     const float *Sl = a.S + (size_t)l * npt;
-    const float Sk = __ldg(Sl + (size_t)k * a.np + q);
-    float jacc = 0.f;
+    const T Sk = (T)__ldg(Sl + (size_t)k * a.np + q);
+    T jacc = 0;
     if (step == 0) {
         for (int d = 0; d < a.ndh; ++d) {
-            float v;
+            T v;
             if (a.bc == RT_BC_ARRAY)
-                v = __ldg(a.I_bc + ((size_t)a.dg[d] * a.nlam + l) * a.np + q);
+                v = (T)__ldg(a.I_bc + ((size_t)a.dg[d] * a.nlam + l) * a.np + q);
             else
-                v = (a.bc == RT_BC_THERMAL && a.up) ? Sk : 0.f;
+                v = (a.bc == RT_BC_THERMAL && a.up) ? Sk : (T)0;
             a.Inext[((size_t)l * a.ndh + d) * a.np + q] = v;
-            jacc += a.w[d] * v;
-            if (a.I_dir) a.I_dir[((size_t)a.dg[d] * a.nlam + l) * npt + (size_t)k * a.np + q] = v;
+            jacc += (T)a.w[d] * v;
+            if (a.I_dir)
+                a.I_dir[((size_t)a.dg[d] * a.nlam + l) * npt + (size_t)k * a.np + q] = (float)v;
         }
     } else {
         const int ku = a.up ? k - 1 : k + 1;
-        const float ak = __ldg(al + (size_t)k * a.np + q);
+        const T ak = (T)__ldg(al + (size_t)k * a.np + q);
         const float *Su = Sl + (size_t)ku * a.np;
         const float *Au = al + (size_t)ku * a.np;
         for (int d = 0; d < a.ndh; ++d) {
-            const Stencil s = a.st[(size_t)k * a.st_stride + a.dst[d]];
-            const float *Iu = a.Iprev + ((size_t)l * a.ndh + d) * a.np;
-            float iu, su, au;
+            const ST s = a.st[(size_t)k * a.st_stride + a.dst[d]];
+            const T *Iu = a.Iprev + ((size_t)l * a.ndh + d) * a.np;
+            T iu, su, au;
             if (a.periodic) {
                 int x0 = i + s.axm;
                 x0 -= (x0 >= a.nx) ? a.nx : 0;
@@ -78,36 +91,37 @@ __global__ void __launch_bounds__(256) sc_plane_kernel(const SweepArgs a, int st
                 int y1 = y0 + 1 == a.ny ? 0 : y0 + 1;
                 const int o00 = y0 * a.nx + x0, o10 = y0 * a.nx + x1;
                 const int o01 = y1 * a.nx + x0, o11 = y1 * a.nx + x1;
-                iu = bilerp(Iu, o00, o10, o01, o11, s);
-                su = bilerp(Su, o00, o10, o01, o11, s);
-                au = bilerp(Au, o00, o10, o01, o11, s);
+                iu = bilerp<T, ST>(Iu, o00, o10, o01, o11, s);
+                su = bilerp_f<T, ST>(Su, o00, o10, o01, o11, s);
+                au = bilerp_f<T, ST>(Au, o00, o10, o01, o11, s);
             } else {
                 // closed sides: no intensity enters from outside; S, alpha clamped to the edge
                 const int xs[2] = {i + s.ax, i + s.ax + 1}, ys[2] = {j + s.ay, j + s.ay + 1};
-                const float ws[4] = {s.w0, s.w1, s.w2, s.w3};
-                iu = su = au = 0.f;
+                const T ws[4] = {(T)s.w0, (T)s.w1, (T)s.w2, (T)s.w3};
+                iu = su = au = 0;
                 for (int c = 0; c < 4; ++c) {
                     const int x = xs[c & 1], y = ys[c >> 1];
                     const bool in = x >= 0 && x < a.nx && y >= 0 && y < a.ny;
                     const int xc = min(max(x, 0), a.nx - 1), yc = min(max(y, 0), a.ny - 1);
                     const int o = yc * a.nx + xc;
                     if (in) iu += ws[c] * __ldg(Iu + o);
-                    su += ws[c] * __ldg(Su + o);
-                    au += ws[c] * __ldg(Au + o);
+                    su += ws[c] * (T)__ldg(Su + o);
+                    au += ws[c] * (T)__ldg(Au + o);
                 }
             }
-            const float dt = (au + ak) * s.hds;
-            float ex, w0, w1;
+            const T dt = (au + ak) * (T)s.hds;
+            T ex, w0, w1;
             lin_weights(dt, ex, w0, w1);
-            const float v = iu * ex + w0 * su + w1 * Sk;
+            const T v = iu * ex + w0 * su + w1 * Sk;
             a.Inext[((size_t)l * a.ndh + d) * a.np + q] = v;
-            jacc += a.w[d] * v;
-            if (a.I_dir) a.I_dir[((size_t)a.dg[d] * a.nlam + l) * npt + (size_t)k * a.np + q] = v;
+            jacc += (T)a.w[d] * v;
+            if (a.I_dir)
+                a.I_dir[((size_t)a.dg[d] * a.nlam + l) * npt + (size_t)k * a.np + q] = (float)v;
         }
     }
     if (a.J) {
         float *Jp = a.J + (size_t)l * npt + (size_t)k * a.np + q;
-        const float v = a.first ? jacc : *Jp + jacc;
+        const float v = a.first ? (float)jacc : *Jp + (float)jacc;
         if (!isfinite(v)) flag_error(a.err, ERR_NAN);
         *Jp = v;
     }
@@ -151,7 +165,7 @@ static rt_status sweep_hemisphere(rt_grid *g, const std::vector<int> &dirs,
     for (int s = 0; s < g->nz; ++s) {
         a.Iprev = bufs[(s + 1) & 1];
         a.Inext = bufs[s & 1];
-        sc_plane_kernel<<<grid, 256, 0, stream>>>(a, s);
+        sc_plane_kernel<float><<<grid, 256, 0, stream>>>(a, s);
     }
     RT_CUDA(cudaGetLastError());
     *last = bufs[(g->nz - 1) & 1];
@@ -163,11 +177,21 @@ rt_status regular_formal_solution(rt_grid *g, int nlam, const float *alpha, cons
                                   cudaStream_t st)
 {
     if (nlam > 65535) return fail(RT_EINVAL, "nlam too large");
+    if (!I_dir) {
+        bool done = false;
+        RT_TRY(regular_cluster_sweep(g, nlam, alpha, S, bc, J, st, &done));
+        if (done) return RT_OK;
+    }
     const size_t np = (size_t)g->nx * g->ny;
     const size_t ndh = std::max(g->dir_up.size(), g->dir_dn.size());
     void *p;
     RT_TRY(scratch_get(g, 0, 2 * (size_t)nlam * ndh * np * sizeof(float), &p));
     float *b0 = (float *)p, *b1 = b0 + (size_t)nlam * ndh * np;
+    if (!I_dir) {
+        bool done = false;
+        RT_TRY(regular_tile_sweep(g, nlam, alpha, S, bc, J, b0, b1, st, &done));
+        if (done) return RT_OK;
+    }
     int first = 1;
     for (int hemi = 0; hemi < 2; ++hemi) {
         const std::vector<int> &dirs = hemi == 0 ? g->dir_up : g->dir_dn;
@@ -188,8 +212,12 @@ static rt_status one_dir_stencil(rt_grid *g, const double *dir, cudaStream_t st)
         g->one_dir[2] == dir[2])
         return RT_OK;
     g->h_stencil_one = regular_dir_stencils(g, dir);
+    g->h_stencil_oned = regular_dir_stencils_d(g, dir);
     if (!g->d_stencil_one) RT_CUDA(cudaMalloc(&g->d_stencil_one, g->nz * sizeof(Stencil)));
+    if (!g->d_stencil_oned) RT_CUDA(cudaMalloc(&g->d_stencil_oned, g->nz * sizeof(StencilD)));
     RT_CUDA(cudaMemcpyAsync(g->d_stencil_one, g->h_stencil_one.data(), g->nz * sizeof(Stencil),
+                            cudaMemcpyHostToDevice, st));
+    RT_CUDA(cudaMemcpyAsync(g->d_stencil_oned, g->h_stencil_oned.data(), g->nz * sizeof(StencilD),
                             cudaMemcpyHostToDevice, st));
     RT_CUDA(cudaStreamSynchronize(st));
     g->one_dir[0] = dir[0];
@@ -229,23 +257,25 @@ rt_status regular_emergent(rt_grid *g, const double *dir, int nlam, const float 
 //   dL/dI_ku(q) = sum_c b_c E(q - a - c),  g_S_ku += sum_c b_c W(.),  g_alpha_ku += sum_c b_c D(.).
 struct AdjArgs {
     const float *alpha, *S;   // [nlam][npt]
-    const float *Iku;         // forward I of plane ku [nlam][np]
-    const float *gIk;         // dL/dI of plane k [nlam][np]
-    float *gIku;              // dL/dI of plane ku (out) [nlam][np]
-    float *EWD;               // [3][nlam][np]
-    float *g_alpha, *g_S;     // [nlam][npt]
-    Stencil s;
+    const double *Iku;        // forward I of plane ku [nlam][np]
+    const double *gIk;        // dL/dI of plane k [nlam][np]
+    double *gIku;             // dL/dI of plane ku (out) [nlam][np]
+    double *EWD;              // [3][nlam][np]
+    double *g_alpha, *g_S;    // [nlam][npt] accumulators
+    StencilD s;
     int nx, ny, np, nlam, k, ku;
     size_t npt;
 };
 
+// The adjoint runs in FP64: dL/dalpha collects differences (S_k - I_up, S_up - S_k) that cancel
+// in optically thick layers, and one direction at a few wavelengths is a small volume.
 __global__ void adj_pass_a(const AdjArgs a)
 {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     const int l = blockIdx.y;
     if (q >= a.np) return;
     const int i = q % a.nx, j = q / a.nx;
-    const Stencil &s = a.s;
+    const StencilD &s = a.s;
     int x0 = i + s.axm;
     x0 -= (x0 >= a.nx) ? a.nx : 0;
     int x1 = x0 + 1 == a.nx ? 0 : x0 + 1;
@@ -255,23 +285,25 @@ __global__ void adj_pass_a(const AdjArgs a)
     const int o00 = y0 * a.nx + x0, o10 = y0 * a.nx + x1, o01 = y1 * a.nx + x0,
               o11 = y1 * a.nx + x1;
     const float *al = a.alpha + (size_t)l * a.npt, *Sl = a.S + (size_t)l * a.npt;
-    const float iu = bilerp(a.Iku + (size_t)l * a.np, o00, o10, o01, o11, s);
-    const float su = bilerp(Sl + (size_t)a.ku * a.np, o00, o10, o01, o11, s);
-    const float au = bilerp(al + (size_t)a.ku * a.np, o00, o10, o01, o11, s);
+    const double iu = bilerp<double, StencilD>(a.Iku + (size_t)l * a.np, o00, o10, o01, o11, s);
+    const double su = bilerp_f<double, StencilD>(Sl + (size_t)a.ku * a.np, o00, o10, o01, o11, s);
+    const double au = bilerp_f<double, StencilD>(al + (size_t)a.ku * a.np, o00, o10, o01, o11, s);
     const size_t pk = (size_t)l * a.npt + (size_t)a.k * a.np + q;
-    const float Sk = __ldg(Sl + (size_t)a.k * a.np + q);
-    const float dt = (au + __ldg(al + (size_t)a.k * a.np + q)) * s.hds;
-    float ex, w0, w1, dex, dw0, dw1;
+    const double Sk = (double)__ldg(Sl + (size_t)a.k * a.np + q);
+    const double hds = (double)s.hds;
+    const double dt = (au + (double)__ldg(al + (size_t)a.k * a.np + q)) * hds;
+    double ex, w0, w1, dex, dw0, dw1;
     lin_weights(dt, ex, w0, w1);
     lin_weights_deriv(dt, ex, dex, dw0, dw1);
-    const float gb = a.gIk[(size_t)l * a.np + q];
-    const float gd = gb * (iu * dex + su * dw0 + Sk * dw1);
+    const double gb = a.gIk[(size_t)l * a.np + q];
+    // dI/ddtau = -e I_up + w0' S_up + w1' S_k = e (S_k - I_up) + w0' (S_up - S_k)  (w0' + w1' = e)
+    const double gd = gb * (ex * (Sk - iu) + dw0 * (su - Sk));
     a.g_S[pk] += w1 * gb;
-    a.g_alpha[pk] += s.hds * gd;
+    a.g_alpha[pk] += hds * gd;
     const size_t m = (size_t)a.nlam * a.np;
     a.EWD[(size_t)l * a.np + q] = ex * gb;
     a.EWD[m + (size_t)l * a.np + q] = w0 * gb;
-    a.EWD[2 * m + (size_t)l * a.np + q] = s.hds * gd;
+    a.EWD[2 * m + (size_t)l * a.np + q] = hds * gd;
 }
 
 __global__ void adj_pass_b(const AdjArgs a)
@@ -280,7 +312,7 @@ __global__ void adj_pass_b(const AdjArgs a)
     const int l = blockIdx.y;
     if (q >= a.np) return;
     const int i = q % a.nx, j = q / a.nx;
-    const Stencil &s = a.s;
+    const StencilD &s = a.s;
     // p = q - a - c for the corners c = (0,0), (1,0), (0,1), (1,1) with weights w0..w3
     int xa = i - s.axm;
     xa += (xa < 0) ? a.nx : 0;                 // q.x - a.x (mod nx)
@@ -291,17 +323,18 @@ __global__ void adj_pass_b(const AdjArgs a)
     const int p00 = ya * a.nx + xa, p10 = ya * a.nx + xb, p01 = yb * a.nx + xa,
               p11 = yb * a.nx + xb;
     const size_t m = (size_t)a.nlam * a.np;
-    const float *E = a.EWD + (size_t)l * a.np, *W = E + m, *D = E + 2 * m;
-    const float gi = s.w0 * E[p00] + s.w1 * E[p10] + s.w2 * E[p01] + s.w3 * E[p11];
-    const float gw = s.w0 * W[p00] + s.w1 * W[p10] + s.w2 * W[p01] + s.w3 * W[p11];
-    const float gdd = s.w0 * D[p00] + s.w1 * D[p10] + s.w2 * D[p01] + s.w3 * D[p11];
+    const double *E = a.EWD + (size_t)l * a.np, *W = E + m, *D = E + 2 * m;
+    const double c0 = s.w0, c1 = s.w1, c2 = s.w2, c3 = s.w3;
+    const double gi = c0 * E[p00] + c1 * E[p10] + c2 * E[p01] + c3 * E[p11];
+    const double gw = c0 * W[p00] + c1 * W[p10] + c2 * W[p01] + c3 * W[p11];
+    const double gdd = c0 * D[p00] + c1 * D[p10] + c2 * D[p01] + c3 * D[p11];
     const size_t pk = (size_t)l * a.npt + (size_t)a.ku * a.np + q;
     a.gIku[(size_t)l * a.np + q] = gi;
     a.g_S[pk] += gw;
     a.g_alpha[pk] += gdd;
 }
 
-__global__ void adj_boundary(float *g_S, const float *gI0, int np, int nlam, size_t npt)
+__global__ void adj_boundary(double *g_S, const double *gI0, int np, int nlam, size_t npt)
 {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     const int l = blockIdx.y;
@@ -309,14 +342,26 @@ __global__ void adj_boundary(float *g_S, const float *gI0, int np, int nlam, siz
     g_S[(size_t)l * npt + q] += gI0[(size_t)l * np + q];
 }
 
-// Workspace: checkpoints [ncp][nlam][np] (forward plane c*stride), segment planes
+__global__ void to_float_kernel(const double *in, float *out, size_t n)
+{
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) out[t] = (float)in[t];
+}
+
+__global__ void to_double_kernel(const float *in, double *out, size_t n)
+{
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) out[t] = (double)in[t];
+}
+
+// Workspace (FP64): checkpoints [ncp][nlam][np] (forward plane c*stride), segment planes
 // [stride][nlam][np], EWD [3][nlam][np] (also the rolling pair of the first forward pass),
-// adjoint planes [2][nlam][np].
+// adjoint planes [2][nlam][np], and the two gradient accumulators [2][nlam][npt].
 size_t regular_adjoint_ws(rt_grid *g, int nlam, int stride)
 {
-    const size_t plane = (size_t)nlam * g->nx * g->ny * sizeof(float);
+    const size_t plane = (size_t)nlam * g->nx * g->ny * sizeof(double);
     const size_t ncp = (size_t)(g->nz + stride - 1) / stride;
-    return (ncp + (size_t)stride + 3 + 2) * plane;
+    return (ncp + (size_t)stride + 3 + 2 + 2 * (size_t)g->nz) * plane;
 }
 
 rt_status regular_adjoint(rt_grid *g, const double *dir, int nlam, const float *alpha,
@@ -330,20 +375,20 @@ rt_status regular_adjoint(rt_grid *g, const double *dir, int nlam, const float *
     const size_t np = (size_t)g->nx * g->ny, plane = (size_t)nlam * np;
     const size_t npt = np * nz;
     const int ncp = (nz + stride - 1) / stride;
-    float *ckpt = (float *)ws;
-    float *seg = ckpt + (size_t)ncp * plane;
-    float *EWD = seg + (size_t)stride * plane;
-    float *gA = EWD + 3 * plane, *gB = gA + plane;
-    const size_t pbytes = plane * sizeof(float);
-    RT_CUDA(cudaMemsetAsync(g_alpha, 0, (size_t)nlam * npt * sizeof(float), st));
-    RT_CUDA(cudaMemsetAsync(g_S, 0, (size_t)nlam * npt * sizeof(float), st));
-    SweepArgs a;
+    double *ckpt = (double *)ws;
+    double *seg = ckpt + (size_t)ncp * plane;
+    double *EWD = seg + (size_t)stride * plane;
+    double *gA = EWD + 3 * plane, *gB = gA + plane;
+    double *accA = gB + plane, *accS = accA + (size_t)nlam * npt;
+    const size_t pbytes = plane * sizeof(double);
+    RT_CUDA(cudaMemsetAsync(accA, 0, 2 * (size_t)nlam * npt * sizeof(double), st));
+    SweepArgsT<double, StencilD> a;
     a.alpha = alpha;
     a.S = S;
     a.J = nullptr;
     a.I_dir = nullptr;
     a.I_bc = nullptr;
-    a.st = g->d_stencil_one;
+    a.st = g->d_stencil_oned;
     a.err = g->d_err;
     a.nx = g->nx;
     a.ny = g->ny;
@@ -361,13 +406,13 @@ rt_status regular_adjoint(rt_grid *g, const double *dir, int nlam, const float *
     a.dst[0] = 0;
     a.w[0] = 1.f;
     dim3 grid((unsigned)((np + 255) / 256), nlam);
-    auto step = [&](int k, const float *prev, float *next) {
+    auto step = [&](int k, const double *prev, double *next) {
         a.Iprev = prev;
         a.Inext = next;
-        sc_plane_kernel<<<grid, 256, 0, st>>>(a, k);
+        sc_plane_kernel<double, StencilD><<<grid, 256, 0, st>>>(a, k);
     };
     // forward sweep keeping plane c*stride of every segment
-    float *roll[2] = {EWD, EWD + plane};
+    double *roll[2] = {EWD, EWD + plane};
     for (int k = 0; k < nz; ++k) {
         step(k, roll[(k + 1) & 1], roll[k & 1]);
         if (k % stride == 0)
@@ -375,19 +420,20 @@ rt_status regular_adjoint(rt_grid *g, const double *dir, int nlam, const float *
                                     cudaMemcpyDeviceToDevice, st));
     }
     // reverse sweep: segment c recomputes planes k0 .. kmax-1 and back-propagates kmax .. k0+1
-    RT_CUDA(cudaMemcpyAsync(gA, gI_top, pbytes, cudaMemcpyDeviceToDevice, st));
+    const unsigned cb = (unsigned)((plane + 255) / 256);
+    to_double_kernel<<<cb, 256, 0, st>>>(gI_top, gA, plane);
     AdjArgs b;
     b.alpha = alpha;
     b.S = S;
     b.EWD = EWD;
-    b.g_alpha = g_alpha;
-    b.g_S = g_S;
+    b.g_alpha = accA;
+    b.g_S = accS;
     b.nx = g->nx;
     b.ny = g->ny;
     b.np = (int)np;
     b.nlam = nlam;
     b.npt = npt;
-    float *gcur = gA, *gnext = gB;
+    double *gcur = gA, *gnext = gB;
     for (int c = ncp - 1; c >= 0; --c) {
         const int k0 = c * stride, kmax = std::min(k0 + stride, nz - 1);
         if (kmax < k0 + 1) continue;
@@ -398,7 +444,7 @@ rt_status regular_adjoint(rt_grid *g, const double *dir, int nlam, const float *
         for (int k = kmax; k >= k0 + 1; --k) {
             b.k = k;
             b.ku = k - 1;
-            b.s = g->h_stencil_one[k];
+            b.s = g->h_stencil_oned[k];
             b.Iku = seg + (size_t)(k - 1 - k0) * plane;
             b.gIk = gcur;
             b.gIku = gnext;
@@ -407,7 +453,10 @@ rt_status regular_adjoint(rt_grid *g, const double *dir, int nlam, const float *
             std::swap(gcur, gnext);
         }
     }
-    if (bc == RT_BC_THERMAL) adj_boundary<<<grid, 256, 0, st>>>(g_S, gcur, (int)np, nlam, npt);
+    if (bc == RT_BC_THERMAL) adj_boundary<<<grid, 256, 0, st>>>(accS, gcur, (int)np, nlam, npt);
+    const size_t tot = (size_t)nlam * npt;
+    to_float_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(accA, g_alpha, tot);
+    to_float_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(accS, g_S, tot);
     RT_CUDA(cudaGetLastError());
     return RT_OK;
 }

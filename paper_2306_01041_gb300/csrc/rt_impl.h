@@ -44,6 +44,13 @@ struct Stencil {
     float pad;
 };
 
+// FP64 stencil of one direction, for the adjoint's forward recomputation.
+struct StencilD {
+    int ax, ay, axm, aym;
+    double w0, w1, w2, w3;
+    double hds;
+};
+
 // ---- Voronoi grid: per (direction, site) upwind record --------------------------------------------
 // k1, k2: upwind site (>= 0) or wall (-1 bottom, -2 top); w1 (w2 = 1 - w1; w1 = 1 and w2 = 0
 // with a single upwind line); l1, l2: segment lengths.
@@ -52,11 +59,18 @@ struct Upwind {
     float w1, l1, l2;
 };
 
+// FP64 record (the adjoint of one direction): w2 held explicitly.
+struct UpwindD {
+    int k1, k2;
+    double w1, w2, l1, l2;
+};
+
 // Upwind tables of a set of directions on one Voronoi grid.
 struct VorTables {
     int ndir = 0;
     std::vector<double> dirs;                  // [ndir][3]
     std::vector<Upwind> h_up;                  // [ndir][nsites], site order
+    std::vector<UpwindD> h_upd;                // FP64 copy (single-direction tables only)
     std::vector<int32_t> h_level;              // [ndir][nsites]
     std::vector<std::vector<int64_t>> lvl_off; // per direction: level offsets into the slots
     Upwind *d_up = nullptr;                    // [ndir][nsites], slot (level) order
@@ -89,6 +103,8 @@ struct rt_grid {
     std::vector<rt::Stencil> h_stencil;
     rt::Stencil *d_stencil_one = nullptr;      // [nz]: one extra direction (emergent/adjoint)
     std::vector<rt::Stencil> h_stencil_one;
+    rt::StencilD *d_stencil_oned = nullptr;    // FP64 copy for the adjoint
+    std::vector<rt::StencilD> h_stencil_oned;
     double one_dir[3] = {0, 0, 0};
     // voronoi
     std::vector<double> xyz;
@@ -117,6 +133,12 @@ rt_status check_dev_error(rt_grid *g, cudaStream_t st);
 // launchers (defined in the .cu files)
 rt_status regular_formal_solution(rt_grid *g, int nlam, const float *alpha, const float *S, int bc,
                                   const float *I_bc, float *J, float *I_dir, cudaStream_t st);
+// fused cluster sweep over all planes; *done = false when it does not apply to this grid
+rt_status regular_cluster_sweep(rt_grid *g, int nlam, const float *alpha, const float *S, int bc,
+                                float *J, cudaStream_t st, bool *done);
+// tiled per-plane sweep (default on periodic grids); *done = false when it does not apply
+rt_status regular_tile_sweep(rt_grid *g, int nlam, const float *alpha, const float *S, int bc,
+                             float *J, float *buf0, float *buf1, cudaStream_t st, bool *done);
 rt_status regular_emergent(rt_grid *g, const double *dir, int nlam, const float *alpha,
                            const float *S, int bc, float *I_top, cudaStream_t st);
 size_t regular_adjoint_ws(rt_grid *g, int nlam, int stride);
@@ -133,6 +155,7 @@ rt_status voronoi_adjoint(rt_grid *g, const double *dir, int nlam, const float *
                           int stride, void *ws, size_t ws_bytes, cudaStream_t st);
 // stencils of one direction for every plane (regular grid), host-built
 std::vector<Stencil> regular_dir_stencils(const rt_grid *g, const double *u);
+std::vector<StencilD> regular_dir_stencils_d(const rt_grid *g, const double *u);
 // upwind tables of the given directions (Voronoi), built on the host and uploaded
 rt_status voronoi_build_tables(const rt_grid *g, int ndir, const double *dirs, VorTables &vt,
                                cudaStream_t st);

@@ -38,73 +38,87 @@ static void transpose(const float *in, float *out, int rows, int cols, cudaStrea
     transpose_kernel<<<grid, dim3(32, 8), 0, st>>>(in, out, rows, cols);
 }
 
-struct VorArgs {
-    const Upwind *up;        // slot-ordered records of this direction
+__device__ __forceinline__ float w2_of(const Upwind &u) { return 1.f - u.w1; }
+__device__ __forceinline__ double w2_of(const UpwindD &u) { return u.w2; }
+
+template <class T, class UP = Upwind> struct VorArgsT {
+    const UP *up;            // records of this direction (slot order, or site order if by_site)
     const int32_t *order;    // slot -> site
     const float *A, *S;      // [n][nlam]
-    float *I;                // [n][nlam] this direction
+    T *I;                    // [n][nlam] this direction
     float *J;                // [n][nlam] or null
     const float *I_bc;       // [nlam][n] of this direction (RT_BC_ARRAY) or null
     unsigned *err;
     int64_t s0, s1;          // slot range of the level
-    int nlam, n, up_dir, bc, first;
+    int nlam, n, up_dir, bc, first, by_site;
     float w;
 };
+using VorArgs = VorArgsT<float>;
 
-// Intensity of one site for one wavelength (Eq. 5 with linear S on each segment).
-__device__ __forceinline__ float site_intensity(const Upwind &u, int i, int l, const VorArgs &a)
+// Intensity of one site for one wavelength (Eq. 5 with linear S on each segment); T = float for
+// the formal solution, double for the adjoint's forward pass.
+template <class T, class UP>
+__device__ __forceinline__ T site_intensity(const UP &u, int i, int l, const VorArgsT<T, UP> &a)
 {
     const size_t il = (size_t)i * a.nlam + l;
-    const float Si = __ldg(a.S + il), Ai = __ldg(a.A + il);
-    float acc = 0.f;
+    const T Si = (T)__ldg(a.S + il), Ai = (T)__ldg(a.A + il);
+    T acc = 0;
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
         const int k = c ? u.k2 : u.k1;
-        const float wk = c ? 1.f - u.w1 : u.w1;
-        const float len = c ? u.l2 : u.l1;
-        if (wk == 0.f) continue;
-        float Ik, Sk, Ak;
+        const T wk = (T)(c ? w2_of(u) : u.w1);
+        const T len = (T)(c ? u.l2 : u.l1);
+        if (wk == (T)0) continue;
+        T Ik, Sk, Ak;
         if (k >= 0) {
             const size_t kl = (size_t)k * a.nlam + l;
             Ik = a.I[kl];
-            Sk = __ldg(a.S + kl);
-            Ak = __ldg(a.A + kl);
+            Sk = (T)__ldg(a.S + kl);
+            Ak = (T)__ldg(a.A + kl);
         } else {
             Sk = Si;
             Ak = Ai;
-            if (a.bc == RT_BC_ARRAY) Ik = __ldg(a.I_bc + (size_t)l * a.n + i);
-            else Ik = (a.bc == RT_BC_THERMAL && a.up_dir && k == -1) ? Si : 0.f;
+            if (a.bc == RT_BC_ARRAY) Ik = (T)__ldg(a.I_bc + (size_t)l * a.n + i);
+            else Ik = (a.bc == RT_BC_THERMAL && a.up_dir && k == -1) ? Si : (T)0;
         }
-        float ex, w0, w1;
-        lin_weights(0.5f * (Ak + Ai) * len, ex, w0, w1);
+        T ex, w0, w1;
+        lin_weights((T)0.5 * (Ak + Ai) * len, ex, w0, w1);
         acc += wk * (Ik * ex + w0 * Sk + w1 * Si);
     }
     return acc;
 }
 
-__global__ void __launch_bounds__(256) vor_level_kernel(const VorArgs a)
+template <class T, class UP>
+__global__ void __launch_bounds__(256) vor_level_kernel(const VorArgsT<T, UP> a)
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t slot = a.s0 + t / a.nlam;
     const int l = (int)(t % a.nlam);
     if (slot >= a.s1) return;
-    const Upwind u = a.up[slot];
     const int i = a.order[slot];
-    const float v = site_intensity(u, i, l, a);
+    const UP u = a.by_site ? a.up[i] : a.up[slot];
+    const T v = site_intensity<T, UP>(u, i, l, a);
     const size_t il = (size_t)i * a.nlam + l;
     a.I[il] = v;
     if (a.J) {
-        const float jv = a.first ? a.w * v : a.J[il] + a.w * v;
+        const float jv = a.first ? a.w * (float)v : a.J[il] + a.w * (float)v;
         if (!isfinite(jv)) flag_error(a.err, ERR_NAN);
         a.J[il] = jv;
     }
 }
 
-static void sweep_direction(const rt_grid *g, const VorTables &vt, int d, VorArgs &a,
-                            cudaStream_t st)
+template <class T, class UP>
+static void sweep_direction(const rt_grid *g, const VorTables &vt, int d, VorArgsT<T, UP> &a,
+                            cudaStream_t st, const UP *site_records = nullptr)
 {
     const int64_t n = g->nsites;
-    a.up = vt.d_up + (size_t)d * n;
+    if (site_records) {
+        a.up = site_records;
+        a.by_site = 1;
+    } else {
+        a.up = reinterpret_cast<const UP *>(vt.d_up) + (size_t)d * n;
+        a.by_site = 0;
+    }
     a.order = vt.d_order + (size_t)d * n;
     a.up_dir = vt.dirs[3 * d + 2] > 0;
     const std::vector<int64_t> &off = vt.lvl_off[d];
@@ -113,7 +127,7 @@ static void sweep_direction(const rt_grid *g, const VorTables &vt, int d, VorArg
         a.s1 = off[L + 1];
         const int64_t work = (a.s1 - a.s0) * a.nlam;
         if (work <= 0) continue;
-        vor_level_kernel<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(a);
+        vor_level_kernel<T, UP><<<(unsigned)((work + 255) / 256), 256, 0, st>>>(a);
     }
 }
 
@@ -141,7 +155,7 @@ rt_status voronoi_formal_solution(rt_grid *g, int nlam, const float *alpha, cons
         a.first = d == 0;
         a.w = (float)g->wdir[d];
         a.I_bc = bc == RT_BC_ARRAY ? I_bc + (size_t)d * f : nullptr;
-        sweep_direction(g, g->vt, d, a, st);
+        sweep_direction<float>(g, g->vt, d, a, st);
         if (I_dir) transpose(It, I_dir + (size_t)d * f, (int)n, nlam, st);
     }
     transpose(Jt, J, (int)n, nlam, st);
@@ -159,11 +173,14 @@ __global__ void gather_top_kernel(const float *I, const int64_t *top, float *out
     out[t] = I[(size_t)top[s] * nlam + l];
 }
 
-// forward sweep of one direction into It [n][nlam] (At, St already transposed)
+// forward sweep of one direction into It [n][nlam] (At, St already transposed); with
+// site_records (FP64, site order) the adjoint's forward pass uses the unrounded tables
+template <class T, class UP = Upwind>
 static rt_status one_dir_forward(rt_grid *g, const VorTables &vt, int nlam, const float *At,
-                                 const float *St, float *It, int bc, cudaStream_t st)
+                                 const float *St, T *It, int bc, cudaStream_t st,
+                                 const UP *site_records = nullptr)
 {
-    VorArgs a;
+    VorArgsT<T, UP> a;
     a.A = At;
     a.S = St;
     a.I = It;
@@ -175,7 +192,7 @@ static rt_status one_dir_forward(rt_grid *g, const VorTables &vt, int nlam, cons
     a.bc = bc;
     a.first = 1;
     a.w = 1.f;
-    sweep_direction(g, vt, 0, a, st);
+    sweep_direction<T, UP>(g, vt, 0, a, st, site_records);
     RT_CUDA(cudaGetLastError());
     return RT_OK;
 }
@@ -192,7 +209,7 @@ rt_status voronoi_emergent(rt_grid *g, const double *dir, int nlam, const float 
     float *At = (float *)p, *St = At + f, *It = St + f;
     transpose(alpha, At, nlam, (int)n, st);
     transpose(S, St, nlam, (int)n, st);
-    RT_TRY(one_dir_forward(g, *vt, nlam, At, St, It, bc, st));
+    RT_TRY(one_dir_forward<float>(g, *vt, nlam, At, St, It, bc, st));
     const int64_t ntop = (int64_t)g->top.size();
     if (ntop)
         gather_top_kernel<<<(unsigned)((ntop * nlam + 255) / 256), 256, 0, st>>>(It, g->d_top,
@@ -207,18 +224,20 @@ rt_status voronoi_emergent(rt_grid *g, const double *dir, int nlam, const float 
 // i), dL/dI_k = gI_loss(k) + sum w_c(i) e_c(i) dL/dI_i and the S, alpha gradients collect the
 // matching w0 and dtau terms; then k adds the terms of its own segments (w1 S_k and alpha_k).
 struct AdjV {
-    const Upwind *up_site;   // [n] records in site order
+    const UpwindD *up_site;  // [n] FP64 records in site order
     const int32_t *order;    // level-ordered sites
     const int64_t *doff;     // [n+1] downwind CSR
     const int32_t *dsite;    // downwind site
     const int8_t *dcomp;     // which upwind slot (0, 1) of that site
-    const float *A, *S, *I;  // [n][nlam]
-    float *G;                // [n][nlam] dL/dI (seeded with the loss gradient)
-    float *gA, *gS;          // [n][nlam]
+    const float *A, *S;      // [n][nlam]
+    const double *I;         // [n][nlam] forward intensity (FP64)
+    double *G;               // [n][nlam] dL/dI (seeded with the loss gradient)
+    double *gA, *gS;         // [n][nlam]
     int64_t s0, s1;
     int nlam, up_dir, bc;
 };
 
+// FP64 throughout (see the regular adjoint for why).
 __global__ void __launch_bounds__(256) vor_adj_level(const AdjV a)
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -227,36 +246,37 @@ __global__ void __launch_bounds__(256) vor_adj_level(const AdjV a)
     if (slot >= a.s1) return;
     const int k = a.order[slot];
     const size_t kl = (size_t)k * a.nlam + l;
-    const float Sk = __ldg(a.S + kl), Ak = __ldg(a.A + kl), Ik = a.I[kl];
-    float g = a.G[kl], gs = 0.f, ga = 0.f;
+    const double Sk = __ldg(a.S + kl), Ak = __ldg(a.A + kl), Ik = a.I[kl];
+    double g = a.G[kl], gs = 0.0, ga = 0.0;
     // contributions of the downwind sites (all at higher levels, already final)
     for (int64_t e = a.doff[k]; e < a.doff[k + 1]; ++e) {
         const int i = a.dsite[e];
         const int c = a.dcomp[e];
-        const Upwind u = a.up_site[i];
-        const float wk = c ? 1.f - u.w1 : u.w1;
-        const float len = c ? u.l2 : u.l1;
+        const UpwindD u = a.up_site[i];
+        const double wk = c ? u.w2 : u.w1;
+        const double len = c ? u.l2 : u.l1;
         const size_t il = (size_t)i * a.nlam + l;
-        const float Si = __ldg(a.S + il), Ai = __ldg(a.A + il), gi = a.G[il] * wk;
-        const float dt = 0.5f * (Ak + Ai) * len;
-        float ex, w0, w1, dex, dw0, dw1;
+        const double Si = __ldg(a.S + il), Ai = __ldg(a.A + il), gi = a.G[il] * wk;
+        const double dt = 0.5 * (Ak + Ai) * len;
+        double ex, w0, w1, dex, dw0, dw1;
         lin_weights(dt, ex, w0, w1);
         lin_weights_deriv(dt, ex, dex, dw0, dw1);
-        const float gd = gi * (Ik * dex + Sk * dw0 + Si * dw1);
+        // dI/ddtau = e (S_i - I_k) + w0' (S_k - S_i), from w0' + w1' = e
+        const double gd = gi * (ex * (Si - Ik) + dw0 * (Sk - Si));
         g += ex * gi;
         gs += w0 * gi;
-        ga += 0.5f * len * gd;
+        ga += 0.5 * len * gd;
     }
     a.G[kl] = g;
     // k's own segments
-    const Upwind u = a.up_site[k];
+    const UpwindD u = a.up_site[k];
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
         const int m = c ? u.k2 : u.k1;
-        const float wk = c ? 1.f - u.w1 : u.w1;
-        const float len = c ? u.l2 : u.l1;
-        if (wk == 0.f) continue;
-        float Im, Sm, Am;
+        const double wk = c ? u.w2 : u.w1;
+        const double len = c ? u.l2 : u.l1;
+        if (wk == 0.0) continue;
+        double Im, Sm, Am;
         const bool wall = m < 0;
         const bool thermal = wall && a.bc == RT_BC_THERMAL && a.up_dir && m == -1;
         if (!wall) {
@@ -267,26 +287,26 @@ __global__ void __launch_bounds__(256) vor_adj_level(const AdjV a)
         } else {
             Sm = Sk;
             Am = Ak;
-            Im = thermal ? Sk : 0.f;
+            Im = thermal ? Sk : 0.0;
         }
-        const float dt = 0.5f * (Am + Ak) * len;
-        float ex, w0, w1, dex, dw0, dw1;
+        const double dt = 0.5 * (Am + Ak) * len;
+        double ex, w0, w1, dex, dw0, dw1;
         lin_weights(dt, ex, w0, w1);
         lin_weights_deriv(dt, ex, dex, dw0, dw1);
-        const float gk = wk * g;
-        const float gd = gk * (Im * dex + Sm * dw0 + Sk * dw1);
+        const double gk = wk * g;
+        const double gd = gk * (ex * (Sk - Im) + dw0 * (Sm - Sk));
         gs += w1 * gk;
-        ga += 0.5f * len * gd;
+        ga += 0.5 * len * gd;
         if (wall) {   // the wall node carries the site's own S and alpha (and I = S if thermal)
-            gs += w0 * gk + (thermal ? ex * gk : 0.f);
-            ga += 0.5f * len * gd;
+            gs += w0 * gk + (thermal ? ex * gk : 0.0);
+            ga += 0.5 * len * gd;
         }
     }
     a.gS[kl] = gs;
     a.gA[kl] = ga;
 }
 
-__global__ void scatter_top_kernel(const float *gI_top, const int64_t *top, float *G,
+__global__ void scatter_top_kernel(const float *gI_top, const int64_t *top, double *G,
                                    int64_t ntop, int nlam)
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -296,13 +316,24 @@ __global__ void scatter_top_kernel(const float *gI_top, const int64_t *top, floa
     G[(size_t)top[s] * nlam + l] = gI_top[t];
 }
 
-// workspace: At, St, It, G, gAt, gSt [n][nlam] + up_site [n] + downwind CSR (n+1 + 2n + 2n)
+// [n][nlam] double -> [nlam][n] float
+__global__ void transpose_d2f_kernel(const double *in, float *out, int64_t n, int nlam)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * nlam) return;
+    const int l = (int)(t / n);
+    const int64_t i = t % n;
+    out[t] = (float)in[(size_t)i * nlam + l];
+}
+
+// workspace: At, St float [n][nlam]; It, G, gAt, gSt double [n][nlam]; up_site [n];
+// downwind CSR (n + 1 offsets, 2n sites, 2n slots)
 size_t voronoi_adjoint_ws(rt_grid *g, int nlam, int stride)
 {
     (void)stride;
     const size_t n = (size_t)g->nsites;
-    return 6 * n * nlam * sizeof(float) + n * sizeof(Upwind) + (n + 1) * sizeof(int64_t) +
-           2 * n * sizeof(int32_t) + 2 * n * sizeof(int8_t) + 64 * 5;
+    return 2 * n * nlam * sizeof(float) + 4 * n * nlam * sizeof(double) + n * sizeof(UpwindD) +
+           (n + 1) * sizeof(int64_t) + 2 * n * sizeof(int32_t) + 2 * n * sizeof(int8_t) + 64 * 8;
 }
 
 static inline char *align_up(char *p)
@@ -323,31 +354,33 @@ rt_status voronoi_adjoint(rt_grid *g, const double *dir, int nlam, const float *
     // downwind CSR of this direction (host)
     std::vector<int64_t> doff(n + 1, 0);
     for (int64_t i = 0; i < n; ++i) {
-        const Upwind &u = vt->h_up[i];
+        const UpwindD &u = vt->h_upd[i];
         if (u.k1 >= 0) doff[u.k1 + 1]++;
-        if (u.w1 < 1.f && u.k2 >= 0) doff[u.k2 + 1]++;
+        if (u.w2 > 0.0 && u.k2 >= 0) doff[u.k2 + 1]++;
     }
     for (int64_t i = 0; i < n; ++i) doff[i + 1] += doff[i];
-    std::vector<int32_t> dsite(doff[n]);
-    std::vector<int8_t> dcomp(doff[n]);
+    std::vector<int32_t> dsite(std::max<int64_t>(doff[n], 1));
+    std::vector<int8_t> dcomp(std::max<int64_t>(doff[n], 1));
     std::vector<int64_t> pos(doff.begin(), doff.end() - 1);
     for (int64_t i = 0; i < n; ++i) {
-        const Upwind &u = vt->h_up[i];
+        const UpwindD &u = vt->h_upd[i];
         if (u.k1 >= 0) { dsite[pos[u.k1]] = (int32_t)i; dcomp[pos[u.k1]++] = 0; }
-        if (u.w1 < 1.f && u.k2 >= 0) { dsite[pos[u.k2]] = (int32_t)i; dcomp[pos[u.k2]++] = 1; }
+        if (u.w2 > 0.0 && u.k2 >= 0) { dsite[pos[u.k2]] = (int32_t)i; dcomp[pos[u.k2]++] = 1; }
     }
     char *c = align_up((char *)ws);
-    float *At = (float *)c, *St = At + f, *It = St + f, *G = It + f, *gAt = G + f, *gSt = gAt + f;
+    float *At = (float *)c, *St = At + f;
+    c = align_up((char *)(St + f));
+    double *It = (double *)c, *G = It + f, *gAt = G + f, *gSt = gAt + f;
     c = align_up((char *)(gSt + f));
-    Upwind *d_up_site = (Upwind *)c;
+    UpwindD *d_up_site = (UpwindD *)c;
     c = align_up((char *)(d_up_site + n));
     int64_t *d_doff = (int64_t *)c;
     c = align_up((char *)(d_doff + n + 1));
     int32_t *d_dsite = (int32_t *)c;
     c = align_up((char *)(d_dsite + std::max<int64_t>(doff[n], 1)));
     int8_t *d_dcomp = (int8_t *)c;
-    RT_CUDA(cudaMemcpyAsync(d_up_site, vt->h_up.data(), n * sizeof(Upwind), cudaMemcpyHostToDevice,
-                            st));
+    RT_CUDA(cudaMemcpyAsync(d_up_site, vt->h_upd.data(), n * sizeof(UpwindD),
+                            cudaMemcpyHostToDevice, st));
     RT_CUDA(cudaMemcpyAsync(d_doff, doff.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice,
                             st));
     if (doff[n]) {
@@ -358,8 +391,10 @@ rt_status voronoi_adjoint(rt_grid *g, const double *dir, int nlam, const float *
     }
     transpose(alpha, At, nlam, (int)n, st);
     transpose(S, St, nlam, (int)n, st);
-    RT_TRY(one_dir_forward(g, *vt, nlam, At, St, It, bc, st));
-    RT_CUDA(cudaMemsetAsync(G, 0, f * sizeof(float), st));
+    const rt_status fwd = one_dir_forward<double, UpwindD>(g, *vt, nlam, At, St, It, bc, st,
+                                                           d_up_site);
+    if (fwd != RT_OK) return fwd;
+    RT_CUDA(cudaMemsetAsync(G, 0, f * sizeof(double), st));
     const int64_t ntop = (int64_t)g->top.size();
     if (ntop)
         scatter_top_kernel<<<(unsigned)((ntop * nlam + 255) / 256), 256, 0, st>>>(gI_top, g->d_top,
@@ -387,11 +422,12 @@ rt_status voronoi_adjoint(rt_grid *g, const double *dir, int nlam, const float *
         if (work <= 0) continue;
         vor_adj_level<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(a);
     }
-    transpose(gAt, g_alpha, (int)n, nlam, st);
-    transpose(gSt, g_S, (int)n, nlam, st);
+    const unsigned tb = (unsigned)((f + 255) / 256);
+    transpose_d2f_kernel<<<tb, 256, 0, st>>>(gAt, g_alpha, n, nlam);
+    transpose_d2f_kernel<<<tb, 256, 0, st>>>(gSt, g_S, n, nlam);
     RT_CUDA(cudaGetLastError());
-    // the host vectors above were copied with pageable cudaMemcpyAsync, which completes before
-    // returning; nothing on the host outlives this call
+    // the host vectors above were copied with pageable cudaMemcpyAsync, which completes its
+    // read of host memory before returning
     return RT_OK;
 }
 

@@ -22,14 +22,19 @@ def rt():
     return rt
 
 
+def f32(x):
+    """The FP32 values the GPU receives, for the oracle to receive the same inputs."""
+    return np.asarray(x, np.float32).astype(np.float64)
+
+
 def _reg_problem(seed=0):
     rng = np.random.default_rng(seed)
     nx, ny, nz, nlam = 21, 17, 24, 3
     z = np.cumsum(np.r_[0.0, 0.5 + rng.random(nz - 1)]) * 0.05
     npt = nx * ny * nz
-    a = 10.0 ** rng.uniform(-1, 1.5, (nlam, npt))
-    s = rng.uniform(0.5, 2.0, (nlam, npt))
-    g = rng.standard_normal((nlam, nx * ny))
+    a = f32(10.0 ** rng.uniform(-1, 1.5, (nlam, npt)))
+    s = f32(rng.uniform(0.5, 2.0, (nlam, npt)))
+    g = f32(rng.standard_normal((nlam, nx * ny)))
     return nx, ny, nz, z, a, s, g
 
 
@@ -48,8 +53,8 @@ def test_regular_adjoint_vs_oracle(rt, mu, bc):
     gI = np.zeros((3, nx * ny * nz))
     gI[:, -nx * ny:] = gtop
     gar, gsr = oracle.sc_regular_adjoint(nx, ny, nz, 0.11, 0.13, z, np.array(mu), a, s, gI, bc=bc)
-    assert_parity(ga.cpu().numpy(), gar, rel=1e-4, floor=1e-5, what="g_alpha")
-    assert_parity(gs.cpu().numpy(), gsr, rel=1e-4, floor=1e-5, what="g_S")
+    assert_parity(ga.cpu().numpy(), gar, rel=1e-4, floor=1e-6, what="g_alpha")
+    assert_parity(gs.cpu().numpy(), gsr, rel=1e-4, floor=1e-6, what="g_S")
 
 
 def test_checkpoint_strides_identical(rt):
@@ -64,40 +69,33 @@ def test_checkpoint_strides_identical(rt):
 
 
 def test_regular_adjoint_vs_finite_differences(rt):
-    """64 random points; central differences of the GPU forward pass in FP32 with a step of
-    3e-3 relative (FP32 rounding ~1e-7 of the loss against truncation ~1e-5)."""
-    import torch
+    """64 random points: the GPU adjoint against central differences (relative step 1e-6) of
+    the FP64 forward model of the same discretisation."""
     nx, ny, nz, z, a, s, gtop = _reg_problem(2)
     dirs, w = s4_quadrature()
     G = rt.RegularGrid(nx, ny, nz, 0.11, 0.13, z, dirs, w)
-    A, S, gt = to_gpu(a), to_gpu(s), to_gpu(gtop)
-    ga, gs = rt.formal_solution_adjoint(G, OBLIQUE, A, S, gt)
+    ga, gs = rt.formal_solution_adjoint(G, OBLIQUE, to_gpu(a), to_gpu(s), to_gpu(gtop))
     ga, gs = ga.cpu().double().numpy(), gs.cpu().double().numpy()
-    scale = max(np.abs(ga).max(), np.abs(gs).max())
+    mu = np.array([OBLIQUE])
 
-    def loss(Ax, Sx):
-        return float((rt.emergent_intensity(G, OBLIQUE, Ax, Sx).double() * gt.double()).sum())
+    def loss(aa, ss):
+        _, I = oracle.sc_regular(nx, ny, nz, 0.11, 0.13, z, mu, np.ones(1), aa, ss, want_I=True)
+        return float((I[0].reshape(3, nz, -1)[:, -1] * gtop).sum())
     rng = np.random.default_rng(3)
-    checked = 0
+    scale = max(np.abs(ga).max(), np.abs(gs).max())
     for _ in range(64):
         l = int(rng.integers(3))
-        top = nx * ny * (nz - 6)
-        p = int(rng.integers(top, nx * ny * nz))   # near the top, where gradients are large
+        p = int(rng.integers(nx * ny * nz))
         for which in (0, 1):
-            base = A if which == 0 else S
-            h = 3e-3 * float(base[l, p])
-            bp, bm = base.clone(), base.clone()
+            base = a if which == 0 else s
+            h = 1e-6 * base[l, p]
+            bp, bm = base.copy(), base.copy()
             bp[l, p] += h
             bm[l, p] -= h
-            if which == 0:
-                fd = (loss(bp, S) - loss(bm, S)) / (2 * h)
-            else:
-                fd = (loss(A, bp) - loss(A, bm)) / (2 * h)
+            fd = ((loss(bp, s) - loss(bm, s)) if which == 0 else
+                  (loss(a, bp) - loss(a, bm))) / (2 * h)
             adj = (ga if which == 0 else gs)[l, p]
-            assert abs(adj - fd) <= 1e-3 * max(abs(fd), 1e-2 * scale), (which, l, p, adj, fd)
-            checked += 1
-    torch.cuda.synchronize()
-    assert checked == 128
+            assert abs(adj - fd) <= 1e-3 * max(abs(fd), 1e-3 * scale), (which, l, p, adj, fd)
 
 
 def test_autograd_function(rt):
@@ -168,9 +166,9 @@ def test_voronoi_adjoint_vs_oracle(rt):
     G = rt.VoronoiGrid(xyz, off, code, shift, box, dirs, w)
     top = G.top_points()
     n, nlam = 600, 3
-    a = 10.0 ** rng.uniform(-0.5, 1.5, (nlam, n))
-    s = rng.uniform(0.5, 2.0, (nlam, n))
-    gtop = rng.standard_normal((nlam, len(top)))
+    a = f32(10.0 ** rng.uniform(-0.5, 1.5, (nlam, n)))
+    s = f32(rng.uniform(0.5, 2.0, (nlam, n)))
+    gtop = f32(rng.standard_normal((nlam, len(top))))
     tab = oracle.voronoi_tables(xyz, off, code, shift, box, np.array([MU1]), 7.0)
     _, Ir = oracle.voronoi_fs(tab, np.array([MU1]), np.ones(1), a, s, want_I=True)
     I_top = rt.emergent_intensity(G, MU1, to_gpu(a), to_gpu(s))
@@ -179,5 +177,5 @@ def test_voronoi_adjoint_vs_oracle(rt):
     gI = np.zeros((nlam, n))
     gI[:, top] = gtop
     gar, gsr = oracle.voronoi_adjoint(tab, 0, True, a, s, gI)
-    assert_parity(ga.cpu().numpy(), gar, rel=1e-4, floor=1e-5, what="Voronoi g_alpha")
-    assert_parity(gs.cpu().numpy(), gsr, rel=1e-4, floor=1e-5, what="Voronoi g_S")
+    assert_parity(ga.cpu().numpy(), gar, rel=1e-4, floor=1e-6, what="Voronoi g_alpha")
+    assert_parity(gs.cpu().numpy(), gsr, rel=1e-4, floor=1e-6, what="Voronoi g_S")
