@@ -213,6 +213,29 @@ rt_status rt_batch_formal_solution(rt_batch_t batch, const float *const *alpha,
                                    const float *const *S, int bc, float *const *J,
                                    void *stream);
 
+/* ---- allocation-free variant -------------------------------------------------------------- */
+/* No counterpart in the paper.  For callers that cannot allocate device memory (host callbacks
+ * and stream-ordered code that must not synchronise the device, plugins whose host application
+ * owns every allocation, processes under a fixed device-memory budget): the regular-grid formal
+ * solution and J of rt_formal_solution (same per-plane sweep), with the grid described directly
+ * by host arrays (as in rt_grid_desc: z[nz], dirs[ndir][3], wdir[ndir]) instead of a grid object,
+ * and its upwind-plane scratch taken from a fixed file-scope device array of 4 Mi floats (16 MiB),
+ * which every GPU that loads the library holds until the process exits.  It calls no cudaMalloc,
+ * cudaFree or allocating library routine.  alpha, S: device [nlam][nx*ny*nz]; J: device output,
+ * overwritten; I_bc: device [ndir][nlam][nx*ny] for RT_BC_ARRAY, else NULL.
+ * Limits: 2 * nlam * (directions per hemisphere) * nx * ny <= 4194304 floats, at most 32
+ * directions per hemisphere; larger problems return RT_EINVAL with a message, before any device
+ * work.  The first call on a device looks up the array's device address (cudaGetSymbolAddress,
+ * with that device current); make that first call before any stream capture.  All calls share
+ * the one array, which keeps the last call's contents (nothing in it needs to start at zero):
+ * calls that overlap on the GPU -- on different streams, or from different host threads --
+ * race on it and must be serialised by the caller.  Asynchronous on `stream`. */
+rt_status rt_formal_solution_regular_noalloc(int nx, int ny, int nz, double dx, double dy,
+                                             const double *z, int periodic_xy, int ndir,
+                                             const double *dirs, const double *wdir, int nlam,
+                                             const float *alpha, const float *S, int bc,
+                                             const float *I_bc, float *J, void *stream);
+
 const char *rt_last_error(void);
 
 /* Host-only diagnostic: G(v) = 2 v F(v) - 1 (F = Dawson's integral) from the double-precision
