@@ -45,6 +45,18 @@ SM_COUNT, LANES, SM_MHZ_MAX = 152, 128, 2070.0
 ALU_PEAK_TFLOPS = SM_COUNT * LANES * 2 * SM_MHZ_MAX * 1e6 / 1e12
 
 
+def max_over_ranks(value, device=None):
+    """The largest value over the ranks of the default process group (the timed region of the
+    slowest replica); the value itself without a group or with one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _env_rank():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
             int(os.environ.get("LOCAL_RANK", "0")))
@@ -147,35 +159,49 @@ def run_gpu(args):
     # One Lambda iteration = source terms -> formal solution (+ J) -> statistical equilibrium ->
     # read-back of max |dn/n|.  The device part is captured once as a CUDA graph and replayed.
     dmax_host = torch.zeros(1, dtype=torch.float32).pin_memory()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
 
-    def body(st):
-        a, s = rt.source_terms(g, atom, atmos, pops, stream=st)
-        alpha.copy_(a)
-        S.copy_(s)
-        ev[0].record(st)
+    def src(st):
+        rt.source_terms(g, atom, atmos, pops, stream=st, out=(alpha, S))
+
+    def fs(st):
         rt.formal_solution(g, alpha, S, J=J, stream=st)
-        ev[1].record(st)
+
+    def se(st):
         d = rt.statistical_equilibrium(g, atom, atmos, J, pops, stream=st)
         dmax_host.copy_(d, non_blocking=True)
 
+    # three graphs so that the formal solution can be timed with events between replays
     cap = torch.cuda.Stream(device=dev)
     cap.wait_stream(torch.cuda.current_stream())
+    graphs = []
     with torch.cuda.stream(cap):
-        body(cap)                      # allocates the library's scratch before capture
+        for part in (src, fs, se):
+            part(cap)                  # allocates the library's scratch before capture
         cap.synchronize()
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph, stream=cap):
-            body(cap)
+        for part in (src, fs, se):
+            gr = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(gr, stream=cap):
+                part(cap)
+            graphs.append(gr)
     torch.cuda.current_stream().wait_stream(cap)
     stream = torch.cuda.current_stream()
     fs_times = []
 
+    part_times = []
+
     def step(record=False):
-        graph.replay()
-        torch.cuda.current_stream().synchronize()   # the convergence read-back
+        ev[2].record(stream)
+        graphs[0].replay()
+        ev[0].record(stream)
+        graphs[1].replay()
+        ev[1].record(stream)
+        graphs[2].replay()
+        ev[3].record(stream)
+        stream.synchronize()           # the convergence read-back
         if record:
             fs_times.append(ev[0].elapsed_time(ev[1]))
+            part_times.append((ev[2].elapsed_time(ev[0]), ev[1].elapsed_time(ev[3])))
         return float(dmax_host.item())
 
     for _ in range(args.warmup):
@@ -196,10 +222,7 @@ def run_gpu(args):
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1) / args.steps
     clk = clocks.stop()
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ms, dev)
     updates = npt * NDIR * nlam
     value = updates * world / (ms * 1e-3) / 1e9
     fs_ms = statistics.mean(fs_times)
@@ -255,6 +278,9 @@ def run_gpu(args):
                      "formal_solution_ms": round(fs_ms, 3),
                      "peak_note": "FP32 lanes x FMA x max clock (152 x 128 x 2 x 2070 MHz)"},
         "clocks": clk,
+        "breakdown_ms": {"source_terms": round(statistics.mean(p[0] for p in part_times), 3),
+                         "formal_solution": round(fs_ms, 3),
+                         "statistical_equilibrium": round(statistics.mean(p[1] for p in part_times), 3)},
     }
     if args.extras:
         res["extras"] = run_extras(torch, rt, dev)
@@ -374,7 +400,8 @@ def run_extras(torch, rt, dev):
     Jp = [torch.empty_like(a) for a in alphas]
     ms_plain = timeit(lambda: [rt.formal_solution(g, a, sv, J=j)
                                for g, a, sv, j in zip(grids, alphas, Ss, Jp)])
-    batch = rt.Batch(grids, nlam)
+    from paper_2306_01041_gb300.autotune import tune_batch
+    batch, choice = tune_batch(grids, alphas, Ss, nlam)
     Jb = [torch.empty_like(a) for a in alphas]
     ms_batch = timeit(lambda: batch.formal_solution(alphas, Ss, Js=Jb))
     diff = max(float(((b - p).abs() / p.abs().clamp_min(1e-30)).max()) for b, p in zip(Jb, Jp))
@@ -384,7 +411,8 @@ def run_extras(torch, rt, dev):
         "plain_ms": round(ms_plain, 2), "batched_ms": round(ms_batch, 2),
         "plain_gupd_s": round(upd / ms_plain / 1e6, 3),
         "batched_gupd_s": round(upd / ms_batch / 1e6, 3),
-        "speedup": round(ms_plain / ms_batch, 2), "max_rel_diff_batched_vs_plain": diff}
+        "speedup": round(ms_plain / ms_batch, 2), "max_rel_diff_batched_vs_plain": diff,
+        "autotuned": choice}
     # one batched Lambda iteration captured as a CUDA graph
     s_cap = torch.cuda.Stream()
     s_cap.wait_stream(torch.cuda.current_stream())

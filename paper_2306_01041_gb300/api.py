@@ -203,10 +203,16 @@ def lte_populations(grid, atom: Atom, atm: Atmos, stream=None):
     return pops
 
 
-def source_terms(grid, atom: Atom, atm: Atmos, pops, stream=None):
+def source_terms(grid, atom: Atom, atm: Atmos, pops, stream=None, out=None):
+    """alpha, S [nlam][npt] from the populations; ``out`` = (alpha, S) to write in place."""
     shp = (atom.nlam, grid.npt)
-    alpha = torch.empty(shp, device="cuda", dtype=torch.float32)
-    S = torch.empty(shp, device="cuda", dtype=torch.float32)
+    if out is None:
+        alpha = torch.empty(shp, device="cuda", dtype=torch.float32)
+        S = torch.empty(shp, device="cuda", dtype=torch.float32)
+    else:
+        alpha, S = out
+        _dev(alpha, shp, "alpha")
+        _dev(S, shp, "S")
     check(lib().rt_source_terms(grid.handle, ctypes.byref(atom.desc), ctypes.byref(atm.desc),
                                 _dev(pops, (3, grid.npt), "pops"), _dev(alpha), _dev(S),
                                 _stream(stream)))

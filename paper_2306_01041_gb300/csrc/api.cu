@@ -438,6 +438,43 @@ rt_status rt_grid_create(const rt_grid_desc *d, void *stream, rt_grid_t *out)
     *out = nullptr;
     if (d->ndir < 1 || d->ndir > MAX_DIR || !d->dirs || !d->wdir)
         return fail(RT_EINVAL, "ndir must be 1..64 with dirs and wdir");
+    // host-side validation first, before any device call
+    if (d->kind == RT_GRID_REGULAR) {
+        if (d->nx < 1 || d->ny < 1 || d->nz < 2 || !(d->dx > 0) || !(d->dy > 0) || !d->z)
+            return fail(RT_EINVAL, "regular grid needs nx, ny >= 1, nz >= 2, dx, dy > 0 and z");
+        for (int k = 1; k < d->nz; ++k)
+            if (!(d->z[k] > d->z[k - 1])) return fail(RT_EINVAL, "z must be strictly ascending");
+    } else if (d->kind == RT_GRID_VORONOI) {
+        if (d->nsites < 1 || !d->xyz || !d->nbr_off || !d->nbr_idx)
+            return fail(RT_EINVAL, "Voronoi grid needs nsites >= 1, xyz, nbr_off and nbr_idx");
+        if (d->nsites > (int64_t)INT32_MAX / 2) return fail(RT_EINVAL, "too many sites");
+        if (!(d->box[1] > d->box[0] && d->box[3] > d->box[2] && d->box[5] > d->box[4]))
+            return fail(RT_EINVAL, "box must have positive extent");
+        if (d->nbr_off[0] != 0) return fail(RT_EINVAL, "nbr_off must start at 0");
+        for (int64_t i = 0; i < d->nsites; ++i)
+            if (d->nbr_off[i + 1] < d->nbr_off[i]) return fail(RT_EINVAL, "nbr_off not monotone");
+        for (int64_t e = 0; e < d->nbr_off[d->nsites]; ++e) {
+            const int64_t c = d->nbr_idx[e];
+            const int64_t k = c >= 0 ? c : ((-c - 1) >> 1);
+            if (k >= d->nsites) return fail(RT_EINVAL, "neighbour index out of range");
+            if (d->nbr_shift && (d->nbr_shift[e] < 0 || d->nbr_shift[e] > 8))
+                return fail(RT_EINVAL, "neighbour image shift out of range");
+        }
+        for (int64_t i = 0; i < d->nsites; ++i)
+            for (int c = 0; c < 3; ++c) {
+                const double v = d->xyz[3 * i + c];
+                if (!std::isfinite(v) || v < d->box[2 * c] || v > d->box[2 * c + 1])
+                    return fail(RT_EINVAL, "site outside the box");
+            }
+    } else {
+        return fail(RT_EINVAL, "unknown grid kind");
+    }
+    for (int q = 0; q < d->ndir; ++q) {
+        const double *u = d->dirs + 3 * q;
+        const double nrm = std::sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        if (!(std::fabs(nrm - 1.0) < 1e-6) || u[2] == 0.0 || !std::isfinite(d->wdir[q]))
+            return fail(RT_EINVAL, "directions must be unit vectors with mu_z != 0");
+    }
     cudaStream_t st = (cudaStream_t)stream;
     rt_grid *g = new (std::nothrow) rt_grid();
     if (!g) return fail(RT_ENOMEM, "host allocation failed");

@@ -7,21 +7,21 @@ namespace rt {
 
 // Linear-S integration over one optical-depth interval d (Sect. 2.5: S linear across the
 // interval; Eq. 2):  I = I_up e^-d + w0 S_up + w1 S with e0 = 1 - e^-d, w1 = (d - e0) / d,
-// w0 = e0 - w1.  Below d = 0.1 the cancellation in d - e0 is avoided by the Taylor series of w1
-// (truncated after d^5, relative error < 1e-9 there); above, e0 comes from the fast exponential.
+// w0 = e0 - w1.  Below d = 0.1 both weights come from their Taylor series (truncated after d^5,
+// relative error < 3e-8): in optically thin layers I can be far below S, so the weights need
+// relative, not just absolute, accuracy.  Above, w1 = 1 - e0 / d with the fast reciprocal
+// (e0 >= 0.095 there, so e0 = 1 - e^-d keeps full relative precision).
 __device__ __forceinline__ void lin_weights(float d, float &ex, float &w0, float &w1)
 {
     ex = __expf(-d);
-    if (d < 0.1f) {
-        // w1 = d/2 - d^2/6 + d^3/24 - d^4/120 + d^5/720
-        w1 = d * (0.5f + d * (-1.0f / 6.0f + d * (1.0f / 24.0f + d * (-1.0f / 120.0f +
-                                                                     d * (1.0f / 720.0f)))));
-        // w0 = e0 - w1, e0 = d - d^2/2 + d^3/6 - d^4/24 + d^5/120
-        w0 = d * (0.5f + d * (-1.0f / 3.0f + d * (1.0f / 8.0f + d * (-1.0f / 30.0f +
-                                                                   d * (1.0f / 144.0f)))));
+    if (d < 0.1f) {   // neighbouring points have similar dtau: the branch is warp-uniform
+        w1 = d * (0.5f + d * (-1.0f / 6.0f + d * (1.0f / 24.0f +
+                                                d * (-1.0f / 120.0f + d * (1.0f / 720.0f)))));
+        w0 = d * (0.5f + d * (-1.0f / 3.0f + d * (1.0f / 8.0f +
+                                                d * (-1.0f / 30.0f + d * (1.0f / 144.0f)))));
     } else {
-        float e0 = 1.0f - ex;
-        w1 = 1.0f - e0 * __frcp_rn(d);
+        const float e0 = 1.0f - ex;
+        w1 = 1.0f - e0 * __fdividef(1.0f, d);
         w0 = e0 - w1;
     }
 }

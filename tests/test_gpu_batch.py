@@ -70,3 +70,23 @@ def test_graph_replay_equals_eager(rt):
     torch.cuda.synchronize()
     for e, j in zip(eager, Js):
         assert torch.equal(e, j)
+
+
+def test_autotuner_choice_is_correct_and_cached(rt, tmp_path, monkeypatch):
+    import importlib
+    monkeypatch.setenv("RT_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    import paper_2306_01041_gb300.autotune as at
+    at = importlib.reload(at)
+    grids = _grids(rt, [300, 900], seed=5)
+    nlam = 5
+    rng = np.random.default_rng(6)
+    alphas = [to_gpu(10.0 ** rng.uniform(-2, 1, (nlam, g.npt))) for g in grids]
+    Ss = [to_gpu(rng.uniform(0.5, 2.0, (nlam, g.npt))) for g in grids]
+    batch, choice = at.tune_batch(grids, alphas, Ss, nlam, candidates=[(1.0, 256), (2.0, 512)])
+    assert (tmp_path / "tune.json").exists() and len(choice["lam_chunk"]) == 2
+    Jb = batch.formal_solution(alphas, Ss)
+    for g, a, s, jb in zip(grids, alphas, Ss, Jb):
+        assert_parity(jb.cpu().numpy(), rt.formal_solution(g, a, s).cpu().numpy().astype(np.float64),
+                      rel=1e-6, what="tuned batch")
+    _, again = at.tune_batch(grids, alphas, Ss, nlam)
+    assert again == choice

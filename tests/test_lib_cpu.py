@@ -53,3 +53,50 @@ def test_dawson_series_matches_scipy(librt):
     got = np.array([librt.rt_debug_G_host(x) for x in v])
     ref = 2 * v * dawsn(v) - 1
     np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-15)
+
+
+def _vor_desc(L, xyz, off, idx, shift, box):
+    d = L.GridDesc()
+    d.kind = L.RT_GRID_VORONOI
+    d.nsites = len(xyz)
+    d.xyz = xyz.ctypes.data_as(L.PD)
+    d.nbr_off = off.ctypes.data_as(L.PI64)
+    d.nbr_idx = idx.ctypes.data_as(L.PI32)
+    d.nbr_shift = shift.ctypes.data_as(L.PI8) if shift is not None else None
+    d.box = (ctypes.c_double * 6)(*box)
+    d.periodic_xy = 1
+    return d
+
+
+@pytest.mark.parametrize("fault", ["index", "shift", "outside", "offsets", "direction"])
+def test_malformed_descriptions_rejected_on_host(librt, fault):
+    """Malformed grids are refused with RT_EINVAL before any device call (runs without a GPU)."""
+    import paper_2306_01041_gb300 as rt
+    from paper_2306_01041_gb300 import _lib as L
+    from synth import delaunay_neighbours, s4_quadrature
+    rng = np.random.default_rng(0)
+    box = (0.0, 1.0, 0.0, 1.0, 0.0, 1.0)
+    xyz = rng.random((60, 3))
+    off, idx, shift = delaunay_neighbours(xyz, box)
+    off, idx, shift = off.copy(), idx.copy(), shift.copy()
+    dirs, w = s4_quadrature()
+    if fault == "index":
+        idx[5] = 60
+    elif fault == "shift":
+        shift[3] = 9
+    elif fault == "outside":
+        xyz[7, 2] = 1.5
+    elif fault == "offsets":
+        off[10] = off[11] + 1
+    else:
+        dirs = dirs.copy()
+        dirs[4] = [1.0, 0.0, 0.0]
+    d = _vor_desc(L, xyz, off, idx, shift, box)
+    d.ndir = len(dirs)
+    dirs = np.ascontiguousarray(dirs)
+    d.dirs = dirs.ctypes.data_as(L.PD)
+    d.wdir = w.ctypes.data_as(L.PD)
+    d.r_exponent = 7.0
+    h = ctypes.c_void_p()
+    assert rt.lib().rt_grid_create(ctypes.byref(d), None, ctypes.byref(h)) == L.RT_EINVAL
+    assert rt.lib().rt_last_error()
