@@ -238,6 +238,11 @@ rt_status rt_formal_solution_regular_noalloc(int nx, int ny, int nz, double dx, 
 
 const char *rt_last_error(void);
 
+/* Number of kernel launches the library has issued in this process (all devices, all threads),
+ * counting launches recorded into a CUDA graph under stream capture once, at capture.  Host-only,
+ * never fails.  The paper has no counterpart: this is instrumentation for benchmarks. */
+unsigned long long rt_kernel_launches(void);
+
 /* Host-only diagnostic: G(v) = 2 v F(v) - 1 (F = Dawson's integral) from the double-precision
  * series that seeds the device Voigt tables; lets CPU tests check the tables' source. */
 double rt_debug_G_host(double v);

@@ -82,6 +82,7 @@ SIGNATURES = {
     "rt_batch_formal_solution": (c_int, [P, ctypes.POINTER(P), ctypes.POINTER(P), c_int,
                                          ctypes.POINTER(P), P]),
     "rt_last_error": (ctypes.c_char_p, []),
+    "rt_kernel_launches": (ctypes.c_ulonglong, []),
 }
 
 

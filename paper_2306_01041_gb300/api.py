@@ -14,6 +14,11 @@ from . import _lib as L
 from ._lib import check, lib
 
 
+def kernel_launches() -> int:
+    """Kernel launches the library has issued in this process (graph captures count once)."""
+    return int(lib().rt_kernel_launches())
+
+
 def _stream(stream=None):
     s = torch.cuda.current_stream() if stream is None else stream
     return ctypes.c_void_p(s.cuda_stream)

@@ -1,9 +1,9 @@
 """Autotuner for the batched persistent Voronoi sweep (rt_batch_create's launch knobs).
 
-The knobs are the wavelength chunk carried by each work item of every grid and the block size
-(warps per level).  Chunks are derived from one scale factor: a grid of n sites gets
-chunk = round(scale * total_sites * nlam / (items_target * n)), which balances the work of the
-items across grids of uneven size.  Every candidate is timed with CUDA events on the caller's
+The knobs are the wavelength chunk carried by each work item (grid, direction, chunk) and the
+block size (warps per level).  Chunks are derived from one scale factor: a grid of n sites gets
+chunk = round(scale * total_sites * nlam * ndir / (items_target * n)), which balances the work of
+the items across grids of uneven size.  Every candidate is timed with CUDA events on the caller's
 inputs (after one warm-up) and the fastest is cached in a JSON file keyed by device name, grid
 sizes, level counts and wavelength count, so later runs reuse it without timing.
 """
@@ -45,7 +45,7 @@ def chunks_for(grids, nlam, scale, items_target):
     total = sum(g.npt for g in grids)
     out = []
     for g in grids:
-        c = int(round(scale * total * nlam / (items_target * g.npt)))
+        c = int(round(scale * total * nlam * g.ndir / (items_target * g.npt)))
         out.append(max(1, min(nlam, c)))
     return out
 
@@ -59,10 +59,10 @@ def tune_batch(grids, alphas, Ss, nlam, candidates=None, reps=2, use_cache=True)
         return Batch(grids, nlam, lam_chunk=c["lam_chunk"], threads=c["threads"]), c
     nsm = torch.cuda.get_device_properties(0).multi_processor_count
     if candidates is None:
-        candidates = [(s, t) for t in (256, 512) for s in (0.5, 1.0, 2.0, 4.0)]
+        candidates = [(s, t) for t in (256, 512) for s in (0.25, 0.5, 1.0, 2.0)]
     best = None
     for scale, threads in candidates:
-        lc = chunks_for(grids, nlam, scale, 2 * nsm)
+        lc = chunks_for(grids, nlam, scale, 4 * nsm)
         b = Batch(grids, nlam, lam_chunk=lc, threads=threads)
         Js = [torch.empty_like(a) for a in alphas]
         b.formal_solution(alphas, Ss, Js=Js)

@@ -1,6 +1,7 @@
 // C ABI entry points of librt.so: error reporting, grid construction (regular-grid stencils,
 // Voronoi upwind tables and dependency levels), and dispatch to the kernels.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -11,6 +12,9 @@
 namespace rt {
 
 static thread_local std::string g_last_error;
+static std::atomic<unsigned long long> g_launches{0};
+
+void note_launch(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 rt_status fail(rt_status st, const std::string &msg)
 {
@@ -431,6 +435,8 @@ rt_grid::~rt_grid()
 extern "C" {
 
 const char *rt_last_error(void) { return g_last_error.c_str(); }
+
+unsigned long long rt_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 rt_status rt_grid_create(const rt_grid_desc *d, void *stream, rt_grid_t *out)
 {

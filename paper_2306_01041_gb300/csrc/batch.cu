@@ -1,11 +1,14 @@
 // Batched persistent sweep over several Voronoi grids of uneven size.
 //
-// Work item = (grid, wavelength chunk).  A block takes an item from a device queue and sweeps all
-// directions of that grid for its wavelengths, level by level, with one __syncthreads between
-// levels; J is summed in direction order by the same block, so the result is deterministic and no
-// block ever waits for another (no co-residency requirement, no device-side spin).  The grid is
-// sized to the number of blocks that fit at once (persistent), and items are queued largest
-// first.  Chunk sizes per grid balance the items' work (sites x chunk).
+// Work item = (grid, direction, wavelength chunk).  A block takes an item from a device queue and
+// sweeps the levels of that direction for its wavelengths, with one __syncthreads between levels;
+// each direction writes its own intensity array, so the 24 directions of a grid run concurrently
+// and the dependent chain of an item is one direction's levels, not all 24 of them.  J is then
+// formed by a reduction over the directions in index order (the same order and arithmetic as the
+// per-direction launches, so the results are identical).  No block ever waits for another: no
+// co-residency requirement and no device-side spin.  The grid is sized to the number of blocks
+// that fit at once (persistent) and items are queued largest first; chunk sizes per grid balance
+// the items' work (sites x chunk).
 #include <algorithm>
 #include <cmath>
 #include <numeric>
@@ -21,13 +24,13 @@ struct BatchGridDev {
     const int64_t *lvl;        // level offsets, all directions concatenated
     const int32_t *lvl_base;   // [ndir + 1] start of each direction's offsets in lvl
     const float *A, *S;        // [n][nlam] transposed inputs
-    float *I, *J;              // [n][nlam]
+    float *I;                  // [ndir][n][nlam] one intensity array per direction
+    float *J;                  // [n][nlam]
     int n;
 };
 
 struct BatchItem {
-    int grid, c0, lc;
-    int pad;
+    int grid, dir, c0, lc;
 };
 
 struct BatchArgs {
@@ -44,60 +47,68 @@ __global__ void __launch_bounds__(512) batch_sweep_kernel(const BatchArgs a)
 {
     __shared__ int item_s;
     for (;;) {
+        __syncthreads();
         if (threadIdx.x == 0) item_s = atomicAdd(a.queue, 1);
         __syncthreads();
         const int it = item_s;
-        __syncthreads();
         if (it >= a.nitems) return;
         const BatchItem item = a.items[it];
         const BatchGridDev g = a.grids[item.grid];
-        for (int d = 0; d < a.ndir; ++d) {
-            const Upwind *up = g.up + (size_t)d * g.n;
-            const int32_t *order = g.order + (size_t)d * g.n;
-            const int b0 = g.lvl_base[d], b1 = g.lvl_base[d + 1];
-            const float w = a.wdir[d];
-            const bool upd = a.up_flag[d] > 0.f;
-            for (int L = b0; L + 1 < b1; ++L) {
-                const int64_t s0 = g.lvl[L], s1 = g.lvl[L + 1];
-                const int64_t work = (s1 - s0) * item.lc;
-                for (int64_t t = threadIdx.x; t < work; t += blockDim.x) {
-                    const int64_t slot = s0 + t / item.lc;
-                    const int l = item.c0 + (int)(t % item.lc);
-                    const Upwind u = up[slot];
-                    const int i = order[slot];
-                    const size_t il = (size_t)i * a.nlam + l;
-                    const float Si = __ldg(g.S + il), Ai = __ldg(g.A + il);
-                    float acc = 0.f;
+        const int d = item.dir;
+        const Upwind *up = g.up + (size_t)d * g.n;
+        const int32_t *order = g.order + (size_t)d * g.n;
+        float *I = g.I + (size_t)d * g.n * a.nlam;
+        const int b0 = g.lvl_base[d], b1 = g.lvl_base[d + 1];
+        const bool upd = a.up_flag[d] > 0.f;
+        for (int L = b0; L + 1 < b1; ++L) {
+            const int64_t s0 = g.lvl[L], s1 = g.lvl[L + 1];
+            const int64_t work = (s1 - s0) * item.lc;
+            for (int64_t t = threadIdx.x; t < work; t += blockDim.x) {
+                const int64_t slot = s0 + t / item.lc;
+                const int l = item.c0 + (int)(t % item.lc);
+                const Upwind u = up[slot];
+                const int i = order[slot];
+                const size_t il = (size_t)i * a.nlam + l;
+                const float Si = __ldg(g.S + il), Ai = __ldg(g.A + il);
+                float acc = 0.f;
 #pragma unroll
-                    for (int c = 0; c < 2; ++c) {
-                        const int k = c ? u.k2 : u.k1;
-                        const float wk = c ? 1.f - u.w1 : u.w1;
-                        const float len = c ? u.l2 : u.l1;
-                        if (wk == 0.f) continue;
-                        float Ik, Sk, Ak;
-                        if (k >= 0) {
-                            const size_t kl = (size_t)k * a.nlam + l;
-                            Ik = g.I[kl];
-                            Sk = __ldg(g.S + kl);
-                            Ak = __ldg(g.A + kl);
-                        } else {
-                            Sk = Si;
-                            Ak = Ai;
-                            Ik = (a.bc == RT_BC_THERMAL && upd && k == -1) ? Si : 0.f;
-                        }
-                        float ex, w0, w1;
-                        lin_weights(0.5f * (Ak + Ai) * len, ex, w0, w1);
-                        acc += wk * (Ik * ex + w0 * Sk + w1 * Si);
+                for (int c = 0; c < 2; ++c) {
+                    const int k = c ? u.k2 : u.k1;
+                    const float wk = c ? 1.f - u.w1 : u.w1;
+                    const float len = c ? u.l2 : u.l1;
+                    if (wk == 0.f) continue;
+                    float Ik, Sk, Ak;
+                    if (k >= 0) {
+                        const size_t kl = (size_t)k * a.nlam + l;
+                        Ik = I[kl];
+                        Sk = __ldg(g.S + kl);
+                        Ak = __ldg(g.A + kl);
+                    } else {
+                        Sk = Si;
+                        Ak = Ai;
+                        Ik = (a.bc == RT_BC_THERMAL && upd && k == -1) ? Si : 0.f;
                     }
-                    g.I[il] = acc;
-                    const float jv = d == 0 ? w * acc : g.J[il] + w * acc;
-                    if (!isfinite(jv)) flag_error(a.err, ERR_NAN);
-                    g.J[il] = jv;
+                    float ex, w0, w1;
+                    lin_weights(0.5f * (Ak + Ai) * len, ex, w0, w1);
+                    acc += wk * (Ik * ex + w0 * Sk + w1 * Si);
                 }
-                __syncthreads();
+                I[il] = acc;
             }
+            __syncthreads();
         }
     }
+}
+
+// J[i][l] = sum_d w_d I_d[i][l], directions in index order
+__global__ void batch_reduce_kernel(const float *I, float *J, const float *wdir, int ndir,
+                                    size_t m, unsigned *err)
+{
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m) return;
+    float acc = wdir[0] * I[t];
+    for (int d = 1; d < ndir; ++d) acc = acc + wdir[d] * I[(size_t)d * m + t];
+    if (!isfinite(acc)) flag_error(err, ERR_NAN);
+    J[t] = acc;
 }
 
 __global__ void transpose_kernel_b(const float *__restrict__ in, float *__restrict__ out, int rows,
@@ -121,6 +132,7 @@ __global__ void transpose_kernel_b(const float *__restrict__ in, float *__restri
 static void transpose_b(const float *in, float *out, int rows, int cols, cudaStream_t st)
 {
     dim3 grid((cols + 31) / 32, (rows + 31) / 32);
+    note_launch();
     transpose_kernel_b<<<grid, dim3(32, 8), 0, st>>>(in, out, rows, cols);
 }
 
@@ -138,7 +150,7 @@ struct rt_batch {
     int64_t *d_lvl = nullptr;
     int32_t *d_lvl_base = nullptr;
     float *d_wdir = nullptr, *d_upf = nullptr;
-    float *d_fields = nullptr;   // per grid A, S, I, J [n][nlam]
+    float *d_fields = nullptr;   // per grid A, S, J [n][nlam] and I [ndir][n][nlam]
     int *d_queue = nullptr;
     unsigned *d_err = nullptr;
     ~rt_batch()
@@ -196,19 +208,20 @@ rt_status rt_batch_create(const rt_grid_t *grids, int ngrids, int nlam, const in
         return fail(RT_ECAPACITY, "the batched sweep kernel cannot be resident");
     }
     b->blocks = nsm * per_sm;
-    // items: default chunk sizes make every item carry about the same number of (site, lambda)
-    // pairs, about total / (2 * resident blocks)
+    // items: default chunk sizes make every item carry about the same number of (site, lambda,
+    // direction) updates, about total / (2 * resident blocks)
     for (int i = 0; i < ngrids; ++i) {
         int lc;
         if (lam_chunk) {
             lc = lam_chunk[i];
         } else {
-            const double target = (double)ntot * nlam / (2.0 * b->blocks);
+            const double target = (double)ntot * nlam * b->ndir / (2.0 * b->blocks);
             lc = (int)std::lround(target / (double)grids[i]->nsites);
         }
         lc = std::max(1, std::min(nlam, lc));
-        for (int c0 = 0; c0 < nlam; c0 += lc)
-            b->h_items.push_back(BatchItem{i, c0, std::min(lc, nlam - c0), 0});
+        for (int d = 0; d < b->ndir; ++d)
+            for (int c0 = 0; c0 < nlam; c0 += lc)
+                b->h_items.push_back(BatchItem{i, d, c0, std::min(lc, nlam - c0)});
     }
     std::stable_sort(b->h_items.begin(), b->h_items.end(), [&](const BatchItem &x, const BatchItem &y) {
         return (double)grids[x.grid]->nsites * x.lc > (double)grids[y.grid]->nsites * y.lc;
@@ -227,7 +240,7 @@ rt_status rt_batch_create(const rt_grid_t *grids, int ngrids, int nlam, const in
         base.push_back((int32_t)lvl.size());
     }
     size_t fsz = 0;
-    for (int i = 0; i < ngrids; ++i) fsz += 4 * (size_t)grids[i]->nsites * nlam;
+    for (int i = 0; i < ngrids; ++i) fsz += (3 + (size_t)b->ndir) * grids[i]->nsites * nlam;
     std::vector<float> wd(b->ndir), uf(b->ndir);
     for (int d = 0; d < b->ndir; ++d) {
         wd[d] = (float)grids[0]->wdir[d];
@@ -262,10 +275,10 @@ rt_status rt_batch_create(const rt_grid_t *grids, int ngrids, int nlam, const in
         gd.lvl_base = b->d_lvl_base + base_at[i];
         gd.A = f;
         gd.S = f + m;
-        gd.I = f + 2 * m;
-        gd.J = f + 3 * m;
+        gd.J = f + 2 * m;
+        gd.I = f + 3 * m;
         gd.n = (int)g->nsites;
-        f += 4 * m;
+        f += (3 + (size_t)b->ndir) * m;
         b->h_grids.push_back(gd);
     }
     BT(cudaMemcpy(b->d_items, b->h_items.data(), b->h_items.size() * sizeof(BatchItem),
@@ -314,9 +327,14 @@ rt_status rt_batch_formal_solution(rt_batch_t b, const float *const *alpha, cons
     a.nlam = b->nlam;
     a.bc = bc;
     const int blocks = std::min<int>(b->blocks, a.nitems);
+    note_launch();
     batch_sweep_kernel<<<blocks, b->threads, 0, st>>>(a);
     for (int i = 0; i < ng; ++i) {
         const BatchGridDev &g = b->h_grids[i];
+        const size_t m = (size_t)g.n * b->nlam;
+        note_launch();
+        batch_reduce_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(g.I, g.J, b->d_wdir,
+                                                                         b->ndir, m, b->d_err);
         transpose_b(g.J, J[i], g.n, b->nlam, st);
     }
     RT_CUDA(cudaGetLastError());

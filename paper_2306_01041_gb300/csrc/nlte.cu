@@ -130,15 +130,17 @@ __device__ inline float val(float a) { return a; }
 __device__ inline float val(Dual a) { return a.v; }
 template <class R> __device__ inline R mk(float v) { return R(v); }
 
-// G(v) for v >= 0: piecewise polynomial on [0, 8), asymptotic series beyond.
-template <class R> __device__ inline R G_eval(R v)
+// G(v) for v >= 0: piecewise polynomial on [0, 8), asymptotic series beyond.  ``tab`` is the
+// block's shared-memory copy of the coefficients: the piece differs from thread to thread, and
+// divergent reads of __constant__ memory would serialise.
+template <class R> __device__ inline R G_eval(R v, const float *tab)
 {
     const float vv = val(v);
     if (vv < 8.0f) {
         int p = min((int)(vv * (G_PIECES / 8.0f)), G_PIECES - 1);
         const float c = (p + 0.5f) * (8.0f / G_PIECES);
         const R t = (v - R(c)) * R(2.0f * G_PIECES / 8.0f);
-        const float *co = c_gpoly + p * G_DEG;
+        const float *co = tab + p * G_DEG;
         R s = R(co[G_DEG - 1]);
         for (int e = G_DEG - 2; e >= 0; --e) s = s * t + R(co[e]);
         return s;
@@ -155,13 +157,21 @@ template <class R> __device__ inline R G_eval(R v)
 }
 
 // Voigt H(a, v) for small a (see the file header)
-template <class R> __device__ inline R voigt_H(float a, R v)
+template <class R> __device__ inline R voigt_H(float a, R v, const float *tab)
 {
     R av = v;
     if (val(v) < 0.f) av = R(0.f) - v;   // H is even in v
     const R v2 = av * av;
     const R e = dexp(R(0.f) - v2);
-    return e * (R(1.f) + R(a * a) * (R(1.f) - R(2.f) * v2)) + R(2.f * a * 0.56418958354775628f) * G_eval(av);
+    return e * (R(1.f) + R(a * a) * (R(1.f) - R(2.f) * v2)) +
+           R(2.f * a * 0.56418958354775628f) * G_eval(av, tab);
+}
+
+// the coefficient table into shared memory (every thread of the block calls this)
+__device__ inline void load_gtab(float *tab)
+{
+    for (int i = threadIdx.x; i < G_PIECES * G_DEG; i += blockDim.x) tab[i] = c_gpoly[i];
+    __syncthreads();
 }
 
 // Planck function B_lambda(T) with x = hc/(lambda k T)
@@ -173,8 +183,8 @@ template <class R> __device__ inline R planck_dev(int j, R T)
 
 // alpha and eta at node j of one point
 template <class R>
-__device__ inline void source_node(int j, R T, R rho, float ne, const float *pops, R phi_norm_inv,
-                                   R dld, R &alpha, R &S)
+__device__ inline void source_node(int j, R T, R rho, float ne, const float *pops, R phi_j,
+                                   R &alpha, R &S)
 {
     const AtomDev &A = c_atom;
     const R t5 = T * R(1.0f / 5000.0f);
@@ -186,9 +196,7 @@ __device__ inline void source_node(int j, R T, R rho, float ne, const float *pop
     const R B = planck_dev<R>(j, T);
     R al = abg, eta = abg * B;
     if (A.kind[j] == 0) {
-        const R v = R(A.dlam[j]) / dld;
-        const R phi = voigt_H<R>(A.a, v) * R(0.56418958354775628f) / dld * phi_norm_inv;
-        const R sig = R(A.c_line) * phi;
+        const R sig = R(A.c_line) * phi_j;
         const R g = R(A.g1_g2) * dexp(R(A.dE_line[j]) / kT);
         al = al + sig * (R(pops[0]) - R(pops[1]) * g);
         eta = eta + sig * R(pops[1]) * g * R(A.b_l5[j]);
@@ -206,31 +214,38 @@ __device__ inline void source_node(int j, R T, R rho, float ne, const float *pop
     S = eta / al;
 }
 
-// 1 / sum_j w_j phi_j over the line nodes (the per-point profile normalisation)
-template <class R> __device__ inline R phi_norm_inv(R dld)
+// The line profile at every line node of one point, normalised so that sum_j w_j phi_j = 1;
+// ph[j] is indexed by the node (entries of continuum nodes are left unset).
+template <class R> __device__ inline void line_profiles(R dld, const float *tab, R *ph)
 {
     R s = R(0.f);
+    const R inv = R(1.f) / dld;
     for (int j = 0; j < c_atom.nlam; ++j) {
         if (c_atom.kind[j] != 0) continue;
-        const R v = R(c_atom.dlam[j]) / dld;
-        s = s + R(c_atom.wline[j]) * voigt_H<R>(c_atom.a, v) * R(0.56418958354775628f) / dld;
+        const R v = R(c_atom.dlam[j]) * inv;
+        ph[j] = voigt_H<R>(c_atom.a, v, tab) * R(0.56418958354775628f) * inv;
+        s = s + R(c_atom.wline[j]) * ph[j];
     }
-    return R(1.f) / s;
+    const R ninv = R(1.f) / s;
+    for (int j = 0; j < c_atom.nlam; ++j)
+        if (c_atom.kind[j] == 0) ph[j] = ph[j] * ninv;
 }
 
 __global__ void source_terms_kernel(int64_t npt, const float *T, const float *rho, const float *ne,
                                     const float *pops, float *alpha, float *S, unsigned *err)
 {
+    __shared__ float tab[G_PIECES * G_DEG];
+    load_gtab(tab);
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= npt) return;
     const float t = T[p], r = rho[p], e = ne[p];
     const float pp[3] = {pops[p], pops[npt + p], pops[2 * npt + p]};
-    const float dld = c_atom.dld_coef * sqrtf(t);
-    const float ninv = phi_norm_inv<float>(dld);
+    float ph[MAX_LAM];
+    line_profiles<float>(c_atom.dld_coef * sqrtf(t), tab, ph);
     bool bad = false;
     for (int j = 0; j < c_atom.nlam; ++j) {
         float a, s;
-        source_node<float>(j, t, r, e, pp, ninv, dld, a, s);
+        source_node<float>(j, t, r, e, pp, c_atom.kind[j] == 0 ? ph[j] : 0.f, a, s);
         alpha[(size_t)j * npt + p] = a;
         S[(size_t)j * npt + p] = s;
         bad |= !isfinite(a) || !isfinite(s);
@@ -243,18 +258,20 @@ __global__ void source_terms_adjoint_kernel(int64_t npt, const float *T, const f
                                             const float *ne, const float *pops, const float *ga,
                                             const float *gs, float *gT)
 {
+    __shared__ float tab[G_PIECES * G_DEG];
+    load_gtab(tab);
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= npt) return;
     const Dual t(T[p], 1.f);
     const Dual r(rho[p], 0.f);
     const float e = ne[p];
     const float pp[3] = {pops[p], pops[npt + p], pops[2 * npt + p]};
-    const Dual dld = Dual(c_atom.dld_coef) * dsqrt(t);
-    const Dual ninv = phi_norm_inv<Dual>(dld);
+    Dual ph[MAX_LAM];
+    line_profiles<Dual>(Dual(c_atom.dld_coef) * dsqrt(t), tab, ph);
     float acc = 0.f;
     for (int j = 0; j < c_atom.nlam; ++j) {
         Dual a, s;
-        source_node<Dual>(j, t, r, e, pp, ninv, dld, a, s);
+        source_node<Dual>(j, t, r, e, pp, c_atom.kind[j] == 0 ? ph[j] : Dual(0.f), a, s);
         acc += ga[(size_t)j * npt + p] * a.d + gs[(size_t)j * npt + p] * s.d;
     }
     gT[p] = acc;
@@ -287,13 +304,15 @@ __global__ void __launch_bounds__(256) se_kernel(int64_t npt, const float *T, co
                                                  const float *nH, const float *J, float *pops,
                                                  float *dmax, unsigned *err)
 {
+    __shared__ float tab[G_PIECES * G_DEG];
+    load_gtab(tab);
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     float change = 0.f;
     if (p < npt) {
         const AtomDev &A = c_atom;
         const float t = T[p], e = ne[p], kT = t * 1.380649e-23f;
-        const float dld = A.dld_coef * sqrtf(t);
-        const float ninv = phi_norm_inv<float>(dld);
+        float ph[MAX_LAM];
+        line_profiles<float>(A.dld_coef * sqrtf(t), tab, ph);
         const float tm32 = 1.f / (t * sqrtf(t));
         float P[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
         for (int j = 0; j < A.nlam; ++j) {
@@ -301,8 +320,7 @@ __global__ void __launch_bounds__(256) se_kernel(int64_t npt, const float *T, co
             float sig, g;
             int lo, hi;
             if (A.kind[j] == 0) {
-                const float v = A.dlam[j] / dld;
-                sig = A.c_line * voigt_H<float>(A.a, v) * 0.56418958354775628f / dld * ninv;
+                sig = A.c_line * ph[j];
                 g = A.g1_g2 * expf(A.dE_line[j] / kT);
                 lo = 0;
                 hi = 1;
@@ -488,6 +506,7 @@ rt_status rt_source_terms_lte(int64_t npt, const float *T, const float *rho, dou
 {
     if (npt < 1 || !T || !rho || !alpha || !S || !(lam > 0)) return fail(RT_EINVAL, "bad argument");
     const double hc = kH * kC;
+    note_launch();
     lte_source_kernel<<<(unsigned)((npt + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
         npt, T, rho, (float)kappa0, (float)(2.0 * hc * kC / std::pow(lam, 5)),
         (float)(hc / (lam * kK)), alpha, S);
@@ -501,6 +520,7 @@ rt_status rt_source_terms_lte_adjoint(int64_t npt, const float *T, const float *
 {
     if (npt < 1 || !T || !rho || !g_alpha || !g_S || !g_T) return fail(RT_EINVAL, "bad argument");
     const double hc = kH * kC;
+    note_launch();
     lte_source_adjoint_kernel<<<(unsigned)((npt + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
         npt, T, rho, (float)kappa0, (float)(2.0 * hc * kC / std::pow(lam, 5)),
         (float)(hc / (lam * kK)), g_alpha, g_S, g_T);
@@ -515,6 +535,7 @@ rt_status rt_source_terms(rt_grid_t g, const rt_atom *atom, const rt_atmos *atm,
     if (!alpha || !S) return fail(RT_EINVAL, "null output");
     RT_TRY(load_atom(atom));
     const int64_t n = g->npt;
+    note_launch();
     source_terms_kernel<<<(unsigned)((n + 127) / 128), 128, 0, (cudaStream_t)stream>>>(
         n, atm->T, atm->rho, atm->ne, pops, alpha, S, g->d_err);
     RT_CUDA(cudaGetLastError());
@@ -529,6 +550,7 @@ rt_status rt_source_terms_adjoint(rt_grid_t g, const rt_atom *atom, const rt_atm
     if (!g_alpha || !g_S || !g_T) return fail(RT_EINVAL, "null argument");
     RT_TRY(load_atom(atom));
     const int64_t n = g->npt;
+    note_launch();
     source_terms_adjoint_kernel<<<(unsigned)((n + 127) / 128), 128, 0, (cudaStream_t)stream>>>(
         n, atm->T, atm->rho, atm->ne, pops, g_alpha, g_S, g_T);
     RT_CUDA(cudaGetLastError());
@@ -541,6 +563,7 @@ rt_status rt_lte_populations(rt_grid_t g, const rt_atom *atom, const rt_atmos *a
     RT_TRY(check_atmos(g, atm, pops));
     RT_TRY(load_atom(atom));
     const int64_t n = g->npt;
+    note_launch();
     lte_pops_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
         n, atm->T, atm->ne, atm->nH, pops);
     RT_CUDA(cudaGetLastError());
@@ -554,6 +577,7 @@ rt_status rt_statistical_equilibrium(rt_grid_t g, const rt_atom *atom, const rt_
     if (!J) return fail(RT_EINVAL, "null J");
     RT_TRY(load_atom(atom));
     const int64_t n = g->npt;
+    note_launch();
     se_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
         n, atm->T, atm->ne, atm->nH, J, pops, dmax_dev, g->d_err);
     RT_CUDA(cudaGetLastError());
@@ -591,9 +615,11 @@ rt_status rt_lambda_iterate(rt_grid_t g, const rt_atom *atom, const rt_atmos *at
     } guard{h_dmax};
     auto enqueue = [&]() -> rt_status {
         RT_CUDA(cudaMemsetAsync(dmax, 0, sizeof(float), st));
+        note_launch();
         source_terms_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(
             n, atm->T, atm->rho, atm->ne, pops, alpha, S, g->d_err);
         RT_TRY(rt_formal_solution(g, nlam, alpha, S, RT_BC_THERMAL, nullptr, J, nullptr, st));
+        note_launch();
         se_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, atm->T, atm->ne, atm->nH, J,
                                                                 pops, dmax, g->d_err);
         RT_CUDA(cudaMemcpyAsync(h_dmax, dmax, sizeof(float), cudaMemcpyDeviceToHost, st));
@@ -614,8 +640,10 @@ rt_status rt_lambda_iterate(rt_grid_t g, const rt_atom *atom, const rt_atmos *at
         // the formal solution allocates its scratch on first use: do that before capturing
         void *q;
         const size_t ndh = std::max(g->dir_up.size(), g->dir_dn.size());
-        if (g->kind == RT_GRID_REGULAR)
+        if (g->kind == RT_GRID_REGULAR) {
             RT_TRY(scratch_get(g, 0, 2 * (size_t)nlam * ndh * g->nx * g->ny * sizeof(float), &q));
+            RT_TRY(scratch_get(g, 3, regular_wave_scratch(g, nlam), &q));
+        }
         else
             RT_TRY(scratch_get(g, 0, 4 * (size_t)n * nlam * sizeof(float), &q));
         RT_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));

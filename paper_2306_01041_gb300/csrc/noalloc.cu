@@ -194,6 +194,7 @@ extern "C" rt_status rt_formal_solution_regular_noalloc(
             a.step = s;
             a.Iprev = bufs[(s + 1) & 1];
             a.Inext = bufs[s & 1];
+            note_launch();
             sc_plane_noalloc_kernel<<<grid, 256, 0, st>>>(a);
         }
         first = 0;

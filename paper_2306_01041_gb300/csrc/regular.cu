@@ -165,6 +165,7 @@ static rt_status sweep_hemisphere(rt_grid *g, const std::vector<int> &dirs,
     for (int s = 0; s < g->nz; ++s) {
         a.Iprev = bufs[(s + 1) & 1];
         a.Inext = bufs[s & 1];
+        note_launch();
         sc_plane_kernel<float><<<grid, 256, 0, stream>>>(a, s);
     }
     RT_CUDA(cudaGetLastError());
@@ -409,6 +410,7 @@ rt_status regular_adjoint(rt_grid *g, const double *dir, int nlam, const float *
     auto step = [&](int k, const double *prev, double *next) {
         a.Iprev = prev;
         a.Inext = next;
+        note_launch();
         sc_plane_kernel<double, StencilD><<<grid, 256, 0, st>>>(a, k);
     };
     // forward sweep keeping plane c*stride of every segment
@@ -421,6 +423,7 @@ rt_status regular_adjoint(rt_grid *g, const double *dir, int nlam, const float *
     }
     // reverse sweep: segment c recomputes planes k0 .. kmax-1 and back-propagates kmax .. k0+1
     const unsigned cb = (unsigned)((plane + 255) / 256);
+    note_launch();
     to_double_kernel<<<cb, 256, 0, st>>>(gI_top, gA, plane);
     AdjArgs b;
     b.alpha = alpha;
@@ -448,14 +451,21 @@ rt_status regular_adjoint(rt_grid *g, const double *dir, int nlam, const float *
             b.Iku = seg + (size_t)(k - 1 - k0) * plane;
             b.gIk = gcur;
             b.gIku = gnext;
+            note_launch();
             adj_pass_a<<<grid, 256, 0, st>>>(b);
+            note_launch();
             adj_pass_b<<<grid, 256, 0, st>>>(b);
             std::swap(gcur, gnext);
         }
     }
-    if (bc == RT_BC_THERMAL) adj_boundary<<<grid, 256, 0, st>>>(accS, gcur, (int)np, nlam, npt);
+    if (bc == RT_BC_THERMAL) {
+        note_launch();
+        adj_boundary<<<grid, 256, 0, st>>>(accS, gcur, (int)np, nlam, npt);
+    }
     const size_t tot = (size_t)nlam * npt;
+    note_launch();
     to_float_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(accA, g_alpha, tot);
+    note_launch();
     to_float_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(accS, g_S, tot);
     RT_CUDA(cudaGetLastError());
     return RT_OK;

@@ -260,6 +260,7 @@ rt_status regular_cluster_sweep(rt_grid *g, int nlam, const float *alpha, const 
     if (maxc < 1) return RT_OK;   // cannot be resident: fall back
     const int ncl = std::min(maxc, nlam);
     cfg.gridDim = dim3(C * ncl);
+    note_launch();
     RT_CUDA(cudaLaunchKernelEx(&cfg, sc_cluster_kernel, a));
     *done = true;
     return RT_OK;

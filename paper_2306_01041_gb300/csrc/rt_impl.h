@@ -25,6 +25,9 @@ rt_status cuda_fail(cudaError_t e, const char *what);
         if (s_ != RT_OK) return s_;                                   \
     } while (0)
 
+// process-wide count of kernel launches issued by the library (also those recorded into a graph)
+void note_launch(unsigned n = 1);
+
 inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 // device error word bits (rt::DevErr in the grid)
@@ -139,6 +142,7 @@ rt_status regular_cluster_sweep(rt_grid *g, int nlam, const float *alpha, const 
 // tiled per-plane sweep (default on periodic grids); *done = false when it does not apply
 rt_status regular_tile_sweep(rt_grid *g, int nlam, const float *alpha, const float *S, int bc,
                              float *J, float *buf0, float *buf1, cudaStream_t st, bool *done);
+size_t regular_wave_scratch(const rt_grid *g, int nlam);
 rt_status regular_emergent(rt_grid *g, const double *dir, int nlam, const float *alpha,
                            const float *S, int bc, float *I_top, cudaStream_t st);
 size_t regular_adjoint_ws(rt_grid *g, int nlam, int stride);

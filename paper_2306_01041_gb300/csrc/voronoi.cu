@@ -35,6 +35,7 @@ __global__ void transpose_kernel(const float *__restrict__ in, float *__restrict
 static void transpose(const float *in, float *out, int rows, int cols, cudaStream_t st)
 {
     dim3 grid((cols + 31) / 32, (rows + 31) / 32);
+    note_launch();
     transpose_kernel<<<grid, dim3(32, 8), 0, st>>>(in, out, rows, cols);
 }
 
@@ -127,6 +128,7 @@ static void sweep_direction(const rt_grid *g, const VorTables &vt, int d, VorArg
         a.s1 = off[L + 1];
         const int64_t work = (a.s1 - a.s0) * a.nlam;
         if (work <= 0) continue;
+        note_launch();
         vor_level_kernel<T, UP><<<(unsigned)((work + 255) / 256), 256, 0, st>>>(a);
     }
 }
@@ -211,9 +213,11 @@ rt_status voronoi_emergent(rt_grid *g, const double *dir, int nlam, const float 
     transpose(S, St, nlam, (int)n, st);
     RT_TRY(one_dir_forward<float>(g, *vt, nlam, At, St, It, bc, st));
     const int64_t ntop = (int64_t)g->top.size();
-    if (ntop)
+    if (ntop) {
+        note_launch();
         gather_top_kernel<<<(unsigned)((ntop * nlam + 255) / 256), 256, 0, st>>>(It, g->d_top,
                                                                                  I_top, ntop, nlam);
+    }
     RT_CUDA(cudaGetLastError());
     return RT_OK;
 }
@@ -396,9 +400,11 @@ rt_status voronoi_adjoint(rt_grid *g, const double *dir, int nlam, const float *
     if (fwd != RT_OK) return fwd;
     RT_CUDA(cudaMemsetAsync(G, 0, f * sizeof(double), st));
     const int64_t ntop = (int64_t)g->top.size();
-    if (ntop)
+    if (ntop) {
+        note_launch();
         scatter_top_kernel<<<(unsigned)((ntop * nlam + 255) / 256), 256, 0, st>>>(gI_top, g->d_top,
                                                                                   G, ntop, nlam);
+    }
     AdjV a;
     a.up_site = d_up_site;
     a.order = vt->d_order;
@@ -420,10 +426,13 @@ rt_status voronoi_adjoint(rt_grid *g, const double *dir, int nlam, const float *
         a.s1 = off[L + 1];
         const int64_t work = (a.s1 - a.s0) * nlam;
         if (work <= 0) continue;
+        note_launch();
         vor_adj_level<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(a);
     }
     const unsigned tb = (unsigned)((f + 255) / 256);
+    note_launch();
     transpose_d2f_kernel<<<tb, 256, 0, st>>>(gAt, g_alpha, n, nlam);
+    note_launch();
     transpose_d2f_kernel<<<tb, 256, 0, st>>>(gSt, g_S, n, nlam);
     RT_CUDA(cudaGetLastError());
     // the host vectors above were copied with pageable cudaMemcpyAsync, which completes its

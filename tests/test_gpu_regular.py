@@ -122,16 +122,19 @@ def test_full_size_128cubed_sampled_wavelengths(rt):
     assert_parity(J.cpu().numpy(), Jr, what="J 128^3")
 
 
-@pytest.mark.parametrize("shape,nlam", [((64, 64, 40), 4), ((32, 48, 17), 3), ((128, 128, 24), 2),
-                                        ((40, 24, 9), 2)])
-def test_sweep_variants_match_each_other_and_oracle(rt, monkeypatch, shape, nlam):
-    """The three regular-grid sweeps -- shared-memory tiles per plane (default), thread-block
-    clusters holding whole planes, and the plain per-plane kernel -- compute the same updates:
-    each matches the oracle and the others (up to FMA contraction)."""
+@pytest.mark.parametrize("shape,nlam,uniform", [((64, 64, 40), 4, False), ((32, 48, 17), 3, False),
+                                                ((128, 128, 24), 2, False), ((40, 24, 9), 2, False),
+                                                ((64, 64, 40), 4, True), ((36, 48, 17), 3, True),
+                                                ((16, 16, 5), 2, True), ((96, 40, 33), 5, True)])
+def test_sweep_variants_match_each_other_and_oracle(rt, monkeypatch, shape, nlam, uniform):
+    """The regular-grid sweeps -- the persistent wavefront kernel (default where every plane has
+    the same stencils, i.e. uniform z), shared-memory tiles per plane, thread-block clusters
+    holding whole planes, and the plain per-plane kernel -- compute the same updates: each
+    matches the oracle and the others (up to FMA contraction)."""
     import torch
     nx, ny, nz = shape
     rng = np.random.default_rng(21)
-    z = np.cumsum(np.r_[0.0, 0.3 + rng.random(nz - 1)])
+    z = np.arange(nz) * 0.8 if uniform else np.cumsum(np.r_[0.0, 0.3 + rng.random(nz - 1)])
     dirs, w = s4_quadrature()
     npt = nx * ny * nz
     a = 10.0 ** rng.uniform(-5, 2, (nlam, npt))
@@ -139,14 +142,21 @@ def test_sweep_variants_match_each_other_and_oracle(rt, monkeypatch, shape, nlam
     g = rt.RegularGrid(nx, ny, nz, 0.7, 0.9, z, dirs, w)
     Jr = oracle.sc_regular(nx, ny, nz, 0.7, 0.9, z, dirs, w, a, s)
     out = {}
-    for mode in ("tile", "cluster", "plane"):
-        if mode == "tile":
+    for mode in ("wave", "tile", "cluster", "plane"):
+        if mode == "wave":
             monkeypatch.delenv("RT_REGULAR_SWEEP", raising=False)
         else:
             monkeypatch.setenv("RT_REGULAR_SWEEP", mode)
-        J = rt.formal_solution(g, to_gpu(a), to_gpu(s))
+        ag, sg = to_gpu(a), to_gpu(s)
+        n0 = rt.kernel_launches()
+        J = rt.formal_solution(g, ag, sg)
+        launched = rt.kernel_launches() - n0
         torch.cuda.synchronize()
+        if mode == "wave":
+            # one persistent launch for both hemispheres on uniform z, else per-plane launches
+            assert (launched == 1) == uniform, launched
         out[mode] = J.cpu().numpy().astype(np.float64)
         assert_parity(out[mode], Jr, what=f"{mode} J")
+    assert_parity(out["wave"], out["plane"], rel=2e-6, what="wave vs plane")
     assert_parity(out["tile"], out["plane"], rel=2e-6, what="tile vs plane")
     assert_parity(out["cluster"], out["plane"], rel=2e-6, what="cluster vs plane")

@@ -100,3 +100,13 @@ def test_malformed_descriptions_rejected_on_host(librt, fault):
     h = ctypes.c_void_p()
     assert rt.lib().rt_grid_create(ctypes.byref(d), None, ctypes.byref(h)) == L.RT_EINVAL
     assert rt.lib().rt_last_error()
+
+
+def test_launch_counter_without_gpu(librt):
+    import paper_2306_01041_gb300 as rt
+    a = rt.kernel_launches()
+    assert isinstance(a, int) and a >= 0
+    # a call rejected on the host launches nothing
+    with pytest.raises(rt.RTError):
+        rt.Batch([], 4)
+    assert rt.kernel_launches() == a
