@@ -117,11 +117,17 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def setup_problem(torch, dev):
+def setup_problem(torch, dev, z_stretch=0.0):
     from synth import make_atmosphere, model_atom, s4_quadrature
     from synth.atmosphere import regular_fields
     atm = make_atmosphere(0)
     f, (x, y, z, dx, dy) = regular_fields(NX, NY, NZ, atm)
+    if z_stretch:
+        # non-uniform z: u -> u - a sin(2 pi u) / (2 pi), cell heights (1 -+ a) times uniform
+        u = (np.arange(NZ) + 0.5) / NZ
+        z = atm.zmin + (atm.zmax - atm.zmin) * (u - z_stretch * np.sin(2 * np.pi * u) / (2 * np.pi))
+        Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+        f = {k: v.reshape(-1) for k, v in atm.fields(X, Y, Z).items()}
     data = model_atom(np.min(f["ne"] / np.sqrt(f["T"])))
     dirs, w = s4_quadrature()
     return atm, f, (x, y, z, dx, dy), data, dirs, w
@@ -142,7 +148,7 @@ def run_gpu(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    atm, f, (x, y, z, dx, dy), data, dirs, w = setup_problem(torch, dev)
+    atm, f, (x, y, z, dx, dy), data, dirs, w = setup_problem(torch, dev, args.z_stretch)
     g = rt.RegularGrid(NX, NY, NZ, dx, dy, z, dirs, w)
     atom = rt.Atom(data, atm.kappa0)
     nlam = atom.nlam
@@ -529,11 +535,15 @@ def main():
     ap.add_argument("--cpu-lams", type=int, default=52)
     ap.add_argument("--nx", type=int, default=128,
                     help="grid size per axis (profiling uses smaller cases; the benchmark is 128)")
+    ap.add_argument("--z-stretch", type=float, default=0.0,
+                    help="non-uniform z spacing amplitude a in [0, 1) (cell heights (1 -+ a) dz)")
     args = ap.parse_args()
     global NX, NY, NZ, WORKLOAD
     if args.nx != 128:
         NX = NY = NZ = args.nx
         WORKLOAD = WORKLOAD.replace("128x128x128", f"{NX}x{NY}x{NZ}")
+    if args.z_stretch:
+        WORKLOAD += f", stretched z (a = {args.z_stretch})"
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

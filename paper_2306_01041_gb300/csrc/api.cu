@@ -143,6 +143,7 @@ static rt_status build_regular(rt_grid *g, const rt_grid_desc *d, cudaStream_t s
     RT_CUDA(cudaMalloc(&g->d_stencil, g->h_stencil.size() * sizeof(Stencil)));
     RT_CUDA(cudaMemcpyAsync(g->d_stencil, g->h_stencil.data(), g->h_stencil.size() * sizeof(Stencil),
                             cudaMemcpyHostToDevice, st));
+    RT_TRY(regular_wave_prepare(g, st));
     g->max_levels = g->nz;
     g->top.resize((size_t)g->nx * g->ny);
     std::iota(g->top.begin(), g->top.end(), (int64_t)(g->nz - 1) * g->nx * g->ny);
@@ -424,6 +425,7 @@ rt_grid::~rt_grid()
     if (d_stencil) cudaFree(d_stencil);
     if (d_stencil_one) cudaFree(d_stencil_one);
     if (d_stencil_oned) cudaFree(d_stencil_oned);
+    if (d_wave_st) cudaFree(d_wave_st);
     vt.release();
     vt_one.release();
     if (d_top) cudaFree(d_top);

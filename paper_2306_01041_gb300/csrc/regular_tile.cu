@@ -14,6 +14,7 @@
 // kernel's constant bank.
 #include <algorithm>
 #include <cstdlib>
+#include <cstring>
 #include <string>
 
 #include "device_common.cuh"
@@ -45,6 +46,7 @@ struct TileArgs {
     int off[TL_MAX_DH];       // corner (0,0) displacement in the shared tile: ay * pitch + ax
     float cw[TL_MAX_DH][4];   // bilinear weights
     float hds[TL_MAX_DH];
+    float hds_min;            // min over the directions of hds
 };
 
 __device__ __forceinline__ int wrapi(int v, int n, bool once)
@@ -64,47 +66,142 @@ struct PlaneCtx {
     float *Inext;
 };
 
-// One (tile, wavelength) item of one plane step.  COHERENT selects L2-coherent loads of the
-// upwind intensities (the persistent kernel reads planes written by other blocks of the same
-// launch, which the non-coherent read-only path could serve stale).
-template <int NDH, bool COHERENT>
+// One direction's stencil on one plane for the persistent sweep on non-uniform z (the uniform case
+// keeps these in the kernel's constant bank instead): bilinear weights, half path length,
+// quadrature weight, corner displacement in the staged tile; hds_min is the plane's minimum hds.
+struct WaveSt {
+    float c0, c1, c2, c3;
+    float hds, wd;
+    int off;
+    float hds_min;
+};
+static_assert(sizeof(WaveSt) == 32, "WaveSt is two float4");
+
+// Interval weights for d >= 0.1 only: the same arithmetic as the d >= 0.1 branch of lin_weights.
+__device__ __forceinline__ void lin_weights_thick(float d, float &ex, float &w0, float &w1)
+{
+    ex = __expf(-d);
+    const float e0 = 1.0f - ex;
+    w1 = 1.0f - e0 * __fdividef(1.0f, d);
+    w0 = e0 - w1;
+}
+
+// Per-point updates of one staged item for every direction.  THICK: every interval of the item
+// has d >= 0.1, so only the exact interval weights are evaluated.
+template <int NDH, bool WAVE, bool THICK, bool PP>
+__device__ __forceinline__ void tile_updates(const TileArgs &a, const WaveSt *sts, const float *It,
+                                             const float4 *SA, int tsz, const int (&slot)[TL_PPT],
+                                             const float (&Sk)[TL_PPT], const float (&ak)[TL_PPT],
+                                             const bool (&ok)[TL_PPT], float *In, size_t dstride,
+                                             size_t mstride, float (&jacc)[TL_PPT])
+{
+    const int ndh = NDH > 0 ? NDH : a.ndh;
+#pragma unroll
+    for (int d = 0; d < (NDH > 0 ? NDH : TL_MAX_DH); ++d) {
+        if (NDH == 0 && d >= ndh) break;
+        float c0, c1, c2, c3, hds, wd;
+        int off;
+        if (PP) {   // per-plane stencil from shared memory (two broadcast loads)
+            const float4 q0 = reinterpret_cast<const float4 *>(sts)[2 * d];
+            const float4 q1 = reinterpret_cast<const float4 *>(sts)[2 * d + 1];
+            c0 = q0.x, c1 = q0.y, c2 = q0.z, c3 = q0.w;
+            hds = q1.x, wd = q1.y, off = __float_as_int(q1.z);
+        } else {    // the same stencil on every plane: constant-bank operands
+            c0 = a.cw[d][0], c1 = a.cw[d][1], c2 = a.cw[d][2], c3 = a.cw[d][3];
+            hds = a.hds[d], wd = a.w[d], off = a.off[d];
+        }
+        const float *Id = It + d * tsz;
+#pragma unroll
+        for (int m = 0; m < TL_PPT; ++m) {
+            const int o = slot[m] + off;
+            const float iu = c0 * Id[o] + c1 * Id[o + 1] + c2 * Id[o + TL_PW] + c3 * Id[o + TL_PW + 1];
+            const float4 p0 = SA[o], p1 = SA[o + TL_PW];   // (S, alpha) at x and x + 1
+            const float su = c0 * p0.x + c1 * p0.z + c2 * p1.x + c3 * p1.z;
+            const float au = c0 * p0.y + c1 * p0.w + c2 * p1.y + c3 * p1.w;
+            const float dt = (au + ak[m]) * hds;
+            float ex, w0, w1;
+            if (THICK) lin_weights_thick(dt, ex, w0, w1);
+            else lin_weights(dt, ex, w0, w1);
+            const float v = iu * ex + w0 * su + w1 * Sk[m];
+            if (ok[m]) {
+                float *dst = In + d * dstride + m * mstride;
+                if (WAVE) __stcg(dst, v);
+                else *dst = v;
+            }
+            jacc[m] += wd * v;
+        }
+    }
+}
+
+// One (tile, wavelength) item of one plane step.  WAVE selects the persistent kernel's variant:
+// L2-coherent loads of the upwind intensities (planes written by other blocks of the same launch,
+// which the non-coherent read-only path could serve stale) and its tile-major intensity ring
+// [nlam][ntiles][ndh][TL_H][TL_W]; otherwise the ring is [nlam][ndh][nx * ny].  PP: the plane's
+// stencils come from the table gst (copied to the shared sts), else from the arguments.
+template <int NDH, bool WAVE, bool PP>
 __device__ __forceinline__ void tile_item(const TileArgs &a, const PlaneCtx &c, int l, int tile,
-                                          float *smt)
+                                          int x0, int y0, float *smt, const WaveSt *gst,
+                                          WaveSt *sts)
 {
     const int ndh = NDH > 0 ? NDH : a.ndh;
     const int ph = TL_H + 2 * a.hy;
-    const int tsz = TL_PW * ph;                              // floats per staged tile
+    const int tsz = TL_PW * ph;                              // slots per staged tile
     float *It = smt;                                         // [ndh][ph][TL_PW]
-    float2 *SA = reinterpret_cast<float2 *>(smt + (size_t)ndh * tsz);   // [ph][TL_PW]
+    float4 *SA = reinterpret_cast<float4 *>(smt + (size_t)ndh * tsz);   // [ph][TL_PW]
     const int tid = threadIdx.x;
     const int lx = tid % TL_W, ly = tid / TL_W;              // ly in 0..TL_ROWS-1
     const size_t npt = (size_t)a.np * a.nz;
     const int q4 = TL_PW / 4;                                // float4 per staged row
-    const int x0 = (tile % a.tiles_x) * TL_W, y0 = (tile / a.tiles_x) * TL_H;
     const float *al = a.alpha + (size_t)l * npt, *Sl = a.S + (size_t)l * npt;
     const float *Su = Sl + (size_t)c.ku * a.np, *Au = al + (size_t)c.ku * a.np;
-    // stage the upwind plane (every direction's intensity, and S with alpha), with halo;
-    // a float4 never straddles the periodic seam because nx and x0 - TL_HXP are multiples of 4
+    // stage the upwind plane (every direction's intensity, and S with alpha), with halo; slot x
+    // of SA holds (S, alpha) at x and x + 1.  A float4 never straddles the periodic seam because
+    // nx and x0 - TL_HXP are multiples of 4.  amin: smallest upwind alpha this thread staged.
+    if (PP && tid < NDH * 8)
+        reinterpret_cast<int *>(sts)[tid] = __ldg(reinterpret_cast<const int *>(gst) + tid);
+    const float hds_min = PP ? __ldg(&gst->hds_min) : a.hds_min;
+    float amin = __int_as_float(0x7f800000);
     for (int e = tid; e < ph * q4; e += TL_THREADS) {
         const int r = e / q4, c4 = e % q4;
         const int gy = wrapi(y0 - a.hy + r, a.ny, a.wrap1);
         const int gx = wrapi(x0 - TL_HXP + 4 * c4, a.nx, a.wrap1);
+        const int gx4 = wrapi(gx + 4, a.nx, true);
         const size_t g = (size_t)gy * a.nx + gx;
+        const size_t g4 = (size_t)gy * a.nx + gx4;
         const float4 sv = __ldg(reinterpret_cast<const float4 *>(Su + g));
         const float4 av = __ldg(reinterpret_cast<const float4 *>(Au + g));
-        float4 *sa = reinterpret_cast<float4 *>(SA + r * TL_PW + 4 * c4);
+        const float s4 = __ldg(Su + g4), a4 = __ldg(Au + g4);
+        float4 *sa = SA + r * TL_PW + 4 * c4;
         sa[0] = make_float4(sv.x, av.x, sv.y, av.y);
-        sa[1] = make_float4(sv.z, av.z, sv.w, av.w);
+        sa[1] = make_float4(sv.y, av.y, sv.z, av.z);
+        sa[2] = make_float4(sv.z, av.z, sv.w, av.w);
+        sa[3] = make_float4(sv.w, av.w, s4, a4);
+        amin = fminf(amin, fminf(fminf(av.x, av.y), fminf(av.z, av.w)));
+        const float *src0;
+        size_t dstep;
+        if (WAVE) {
+            const int tt = (gy / TL_H) * a.tiles_x + gx / TL_W;
+            src0 = c.Iprev + (((size_t)l * a.ntiles + tt) * ndh) * (TL_W * TL_H) +
+                   (gy % TL_H) * TL_W + gx % TL_W;
+            dstep = TL_W * TL_H;
+        } else {
+            src0 = c.Iprev + (size_t)l * ndh * a.np + g;
+            dstep = a.np;
+        }
 #pragma unroll
         for (int d = 0; d < (NDH > 0 ? NDH : TL_MAX_DH); ++d) {
             if (NDH == 0 && d >= ndh) break;
-            const float4 *src = reinterpret_cast<const float4 *>(
-                c.Iprev + ((size_t)l * ndh + d) * a.np + g);
-            const float4 iv = COHERENT ? __ldcg(src) : __ldg(src);
+            const float4 *src = reinterpret_cast<const float4 *>(src0 + d * dstep);
+            const float4 iv = WAVE ? __ldcg(src) : __ldg(src);
             reinterpret_cast<float4 *>(It + d * tsz + r * TL_PW)[c4] = iv;
         }
     }
-    __syncthreads();
+    // d = (alpha_up + alpha_k) * hds >= amin * hds_min: the whole item is thick when every
+    // thread's staged alpha clears the bound (the barrier that publishes the tile decides it);
+    // the 1e-4 margin covers the rounding of the interpolated alpha, so that an interval the
+    // general path would send to the series never takes the exact formula
+    const bool thick = __syncthreads_and(amin * hds_min >= 0.1f * 1.0001f);
+    // the item's own points: S and alpha on plane k
     int gxy[TL_PPT], slot[TL_PPT];
     float Sk[TL_PPT], ak[TL_PPT], jacc[TL_PPT];
     bool ok[TL_PPT];
@@ -118,38 +215,30 @@ __device__ __forceinline__ void tile_item(const TileArgs &a, const PlaneCtx &c, 
         ak[m] = ok[m] ? __ldg(al + (size_t)c.k * a.np + gxy[m]) : 0.f;
         jacc[m] = 0.f;
     }
-    float *In = c.Inext + (size_t)l * ndh * a.np;
-#pragma unroll
-    for (int d = 0; d < (NDH > 0 ? NDH : TL_MAX_DH); ++d) {
-        if (NDH == 0 && d >= ndh) break;
-        const float c0 = a.cw[d][0], c1 = a.cw[d][1], c2 = a.cw[d][2], c3 = a.cw[d][3];
-        const float hds = a.hds[d], wd = a.w[d];
-        const float *Id = It + d * tsz;
-#pragma unroll
-        for (int m = 0; m < TL_PPT; ++m) {
-            const int o = slot[m] + a.off[d];
-            const float iu = c0 * Id[o] + c1 * Id[o + 1] + c2 * Id[o + TL_PW] + c3 * Id[o + TL_PW + 1];
-            const float2 s00 = SA[o], s10 = SA[o + 1], s01 = SA[o + TL_PW], s11 = SA[o + TL_PW + 1];
-            const float su = c0 * s00.x + c1 * s10.x + c2 * s01.x + c3 * s11.x;
-            const float au = c0 * s00.y + c1 * s10.y + c2 * s01.y + c3 * s11.y;
-            const float dt = (au + ak[m]) * hds;
-            float ex, w0, w1;
-            lin_weights(dt, ex, w0, w1);
-            const float v = iu * ex + w0 * su + w1 * Sk[m];
-            if (ok[m]) {
-                if (COHERENT) __stcg(In + (size_t)d * a.np + gxy[m], v);
-                else In[(size_t)d * a.np + gxy[m]] = v;
-            }
-            jacc[m] += wd * v;
-        }
+    float *In;
+    size_t dstride, mstride;
+    if (WAVE) {
+        In = c.Inext + ((size_t)l * a.ntiles + tile) * ndh * (TL_W * TL_H) + ly * TL_W + lx;
+        dstride = TL_W * TL_H;
+        mstride = TL_ROWS * TL_W;
+    } else {
+        In = c.Inext + (size_t)l * ndh * a.np + gxy[0];
+        dstride = a.np;
+        mstride = (size_t)TL_ROWS * a.nx;
     }
+    if (thick)
+        tile_updates<NDH, WAVE, true, PP>(a, sts, It, SA, tsz, slot, Sk, ak, ok, In, dstride,
+                                          mstride, jacc);
+    else
+        tile_updates<NDH, WAVE, false, PP>(a, sts, It, SA, tsz, slot, Sk, ak, ok, In, dstride,
+                                           mstride, jacc);
 #pragma unroll
     for (int m = 0; m < TL_PPT; ++m) {
         if (!ok[m]) continue;
         float *Jp = a.J + (size_t)l * npt + (size_t)c.k * a.np + gxy[m];
-        const float v = c.first ? jacc[m] : (COHERENT ? __ldcg(Jp) : *Jp) + jacc[m];
+        const float v = c.first ? jacc[m] : (WAVE ? __ldcg(Jp) : *Jp) + jacc[m];
         if (!isfinite(v)) flag_error(a.err, ERR_NAN);
-        if (COHERENT) __stcg(Jp, v);
+        if (WAVE) __stcg(Jp, v);
         else *Jp = v;
     }
 }
@@ -162,18 +251,21 @@ __global__ void __launch_bounds__(TL_THREADS, 2) sc_tile_kernel(const TileArgs a
     const int nitems = a.ntiles * a.nlam;
     for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
         __syncthreads();   // the previous item's reads of the tile are done
-        tile_item<NDH, false>(a, c, item / a.ntiles, item % a.ntiles, smt);
+        const int l = item / a.ntiles, tile = item % a.ntiles;
+        tile_item<NDH, false, false>(a, c, l, tile, (tile % a.tiles_x) * TL_W,
+                                     (tile / a.tiles_x) * TL_H, smt, nullptr, nullptr);
     }
 }
 
-// Boundary plane of one tile and wavelength: the rule for every direction, and J.
+// Boundary plane of one tile and wavelength (persistent kernel): the rule for every direction
+// into the tile-major ring, and J.
 template <int NDH>
 __device__ __forceinline__ void boundary_item(const TileArgs &a, const PlaneCtx &c, int l, int tile,
-                                              int bc)
+                                              int x0, int y0, int bc)
 {
     const int ndh = NDH > 0 ? NDH : a.ndh;
-    const int x0 = (tile % a.tiles_x) * TL_W, y0 = (tile / a.tiles_x) * TL_H;
     const size_t npt = (size_t)a.np * a.nz;
+    float *In = c.Inext + ((size_t)l * a.ntiles + tile) * ndh * (TL_W * TL_H);
     for (int e = threadIdx.x; e < TL_W * TL_H; e += TL_THREADS) {
         const int x = x0 + e % TL_W, y = y0 + e / TL_W;
         if (x >= a.nx || y >= a.ny) continue;
@@ -182,7 +274,7 @@ __device__ __forceinline__ void boundary_item(const TileArgs &a, const PlaneCtx 
         const float v = (bc == RT_BC_THERMAL && c.up) ? Sk : 0.f;
         float jacc = 0.f;
         for (int d = 0; d < ndh; ++d) {
-            __stcg(c.Inext + ((size_t)l * ndh + d) * a.np + q, v);
+            __stcg(In + (size_t)d * (TL_W * TL_H) + e, v);
             jacc += a.w[d] * v;
         }
         float *Jp = a.J + (size_t)l * npt + (size_t)c.k * a.np + q;
@@ -205,6 +297,7 @@ struct WaveArgs {
     float *ring[2][2];         // [hemisphere][step parity] upwind planes [nlam][ndh][np]
     int *queue;
     int *done;                 // [2][nz][nlam][ntiles] completion flags
+    const WaveSt *st;          // [nz][2][12] per-plane stencils (non-uniform z), else null
     int nd[2];
     int bc, first_hemi;
 };
@@ -224,28 +317,47 @@ __device__ __forceinline__ bool wait_flag(const int *f, const unsigned *err)
     return false;
 }
 
-template <int NDH>
+struct WaveItem {
+    int item, h, s, l, tile, x0, y0, pad;
+};
+
+__device__ __forceinline__ WaveItem wave_decode(const TileArgs &a, int item)
+{
+    const int nt = a.ntiles, nl = a.nlam;
+    const int per_hemi = a.nz * nl * nt;
+    WaveItem it;
+    it.item = item;
+    it.h = item / per_hemi;
+    int rem = item - it.h * per_hemi;
+    it.s = rem / (nl * nt);
+    rem -= it.s * (nl * nt);
+    it.l = rem / nt;
+    it.tile = rem - it.l * nt;
+    it.x0 = (it.tile % a.tiles_x) * TL_W;
+    it.y0 = (it.tile / a.tiles_x) * TL_H;
+    it.pad = 0;
+    return it;
+}
+
+// PP: per-plane stencils from the table (non-uniform z); else the constant-bank stencils.
+template <int NDH, bool PP>
 __global__ void __launch_bounds__(TL_THREADS, 2) sc_wave_kernel(WaveArgs w)
 {
     extern __shared__ __align__(16) float smt[];
-    __shared__ int item_s;
+    __shared__ WaveItem cur;
+    __shared__ __align__(16) WaveSt sts[PP ? NDH : 1];
     const TileArgs &a = w.t[0];
     const int nt = a.ntiles, nl = a.nlam, nz = a.nz;
-    const int per_hemi = nz * nl * nt;
-    const int total = 2 * per_hemi;
+    const int total = 2 * nz * nl * nt;
     const int tx = a.tiles_x, ty = nt / a.tiles_x;
-    if (threadIdx.x == 0) item_s = atomicAdd(w.queue, 1);
+    if (threadIdx.x == 0) cur = wave_decode(a, atomicAdd(w.queue, 1));
     for (;;) {
-        __syncthreads();   // item_s is published; the previous item is finished by every thread
-        const int item = item_s;
-        if (item >= total) return;
+        __syncthreads();   // cur is published; the previous item is finished by every thread
+        const WaveItem it = cur;
+        if (it.item >= total) return;
         int next = 0;
         if (threadIdx.x == 0) next = atomicAdd(w.queue, 1);
-        const int h = item / per_hemi;
-        int rem = item % per_hemi;
-        const int s = rem / (nl * nt);
-        rem %= nl * nt;
-        const int l = rem / nt, tile = rem % nt;
+        const int h = it.h, s = it.s, l = it.l, tile = it.tile;
         const bool up = h == 0;
         const int k = up ? s : nz - 1 - s;
         PlaneCtx c;
@@ -269,19 +381,24 @@ __global__ void __launch_bounds__(TL_THREADS, 2) sc_wave_kernel(WaveArgs w)
             if (lane == 0 && !ok) flag_error(a.err, ERR_TIMEOUT);
         }
         __syncthreads();
-        // one inlined copy per hemisphere keeps every per-direction constant a static operand
-        if (h == 0) {
-            if (s == 0) boundary_item<NDH>(w.t[0], c, l, tile, w.bc);
-            else tile_item<NDH, true>(w.t[0], c, l, tile, smt);
+        if (PP) {
+            // one code copy for both hemispheres: the stencils and weights come from the table
+            if (s == 0) boundary_item<NDH>(w.t[h], c, l, tile, it.x0, it.y0, w.bc);
+            else tile_item<NDH, true, true>(w.t[0], c, l, tile, it.x0, it.y0, smt,
+                                            w.st + ((size_t)k * 2 + h) * NDH, sts);
+        } else if (h == 0) {
+            // one inlined copy per hemisphere keeps every per-direction constant a static operand
+            if (s == 0) boundary_item<NDH>(w.t[0], c, l, tile, it.x0, it.y0, w.bc);
+            else tile_item<NDH, true, false>(w.t[0], c, l, tile, it.x0, it.y0, smt, nullptr, nullptr);
         } else {
-            if (s == 0) boundary_item<NDH>(w.t[1], c, l, tile, w.bc);
-            else tile_item<NDH, true>(w.t[1], c, l, tile, smt);
+            if (s == 0) boundary_item<NDH>(w.t[1], c, l, tile, it.x0, it.y0, w.bc);
+            else tile_item<NDH, true, false>(w.t[1], c, l, tile, it.x0, it.y0, smt, nullptr, nullptr);
         }
         __syncthreads();
         if (threadIdx.x == 0) {
             int *f = w.done + ((size_t)(h * nz + s) * nl + l) * nt + tile;
             asm volatile("st.release.gpu.global.b32 [%0], %1;" :: "l"(f), "r"(1) : "memory");
-            item_s = next;
+            cur = wave_decode(a, next);
         }
     }
 }
@@ -304,10 +421,10 @@ __global__ void sc_tile_boundary_kernel(const TileArgs a, int bc)
     *Jp = a.first ? jacc : *Jp + jacc;
 }
 
-static bool tile_plan(const rt_grid *g, int &hy)
+// The staged tile covers every stencil: periodic x and y, nx a multiple of 4 (16-byte rows),
+// corner reach within the x halo and at most 8 rows in y.
+static bool tile_geometry(const rt_grid *g, int &hy)
 {
-    const char *env = std::getenv("RT_REGULAR_SWEEP");
-    if (env && (std::string(env) == "plane" || std::string(env) == "cluster")) return false;
     if (!g->periodic || g->nx % 4 || g->dir_up.size() > TL_MAX_DH || g->dir_dn.size() > TL_MAX_DH)
         return false;
     // corners reach x + ax .. x + ax + 1 and y + ay .. y + ay + 1
@@ -322,12 +439,19 @@ static bool tile_plan(const rt_grid *g, int &hy)
     return std::max(lx, rx) <= TL_HXP && hy <= 8;
 }
 
+static bool tile_plan(const rt_grid *g, int &hy)
+{
+    const char *env = std::getenv("RT_REGULAR_SWEEP");
+    if (env && (std::string(env) == "plane" || std::string(env) == "cluster")) return false;
+    return tile_geometry(g, hy);
+}
+
 template <int NDH>
 static rt_status launch_planes(rt_grid *g, TileArgs &a, const std::vector<int> &dirs, int bc,
                                int nlam, float **bufs, cudaStream_t st)
 {
     const int ph = TL_H + 2 * a.hy, tsz = TL_PW * ph;
-    const size_t smem = ((size_t)a.ndh * tsz) * sizeof(float) + (size_t)tsz * sizeof(float2);
+    const size_t smem = ((size_t)a.ndh * tsz) * sizeof(float) + (size_t)tsz * sizeof(float4);
     RT_CUDA(cudaFuncSetAttribute(sc_tile_kernel<NDH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
     int per_sm = 0, dev = 0, nsm = 0;
@@ -356,6 +480,7 @@ static rt_status launch_planes(rt_grid *g, TileArgs &a, const std::vector<int> &
             a.cw[d][2] = sc.w2;
             a.cw[d][3] = sc.w3;
             a.hds[d] = sc.hds;
+            a.hds_min = d == 0 ? sc.hds : std::min(a.hds_min, sc.hds);
         }
         note_launch();
         sc_tile_kernel<NDH><<<blocks, TL_THREADS, smem, st>>>(a);
@@ -385,10 +510,44 @@ static bool uniform_stencils(const rt_grid *g)
 
 size_t regular_wave_scratch(const rt_grid *g, int nlam)
 {
-    const size_t plane = (size_t)nlam * 12 * g->nx * g->ny;
     const size_t ntiles = (size_t)((g->nx + TL_W - 1) / TL_W) * ((g->ny + TL_H - 1) / TL_H);
+    const size_t plane = (size_t)nlam * ntiles * 12 * TL_W * TL_H;   // tile-major ring slot
     const size_t nflags = 2 * (size_t)g->nz * nlam * ntiles;
     return 4 * plane * sizeof(float) + (nflags + 64) * sizeof(int);
+}
+
+rt_status regular_wave_prepare(rt_grid *g, cudaStream_t st)
+{
+    int hy;
+    if (!tile_geometry(g, hy) || g->dir_up.size() != 12 || g->dir_dn.size() != 12 || g->nz < 3)
+        return RT_OK;
+    std::vector<WaveSt> t((size_t)g->nz * 2 * 12, WaveSt{0, 0, 0, 0, 0, 0, 0, 0});
+    const std::vector<int> *hs[2] = {&g->dir_up, &g->dir_dn};
+    for (int k = 0; k < g->nz; ++k)
+        for (int h = 0; h < 2; ++h) {
+            if ((h == 0 && k == 0) || (h == 1 && k == g->nz - 1)) continue;   // boundary planes
+            WaveSt *e = &t[((size_t)k * 2 + h) * 12];
+            float hmin = 0.f;
+            for (int d = 0; d < 12; ++d) {
+                const int q = (*hs[h])[d];
+                const Stencil &sc = g->h_stencil[(size_t)k * g->ndir + q];
+                e[d].c0 = sc.w0;
+                e[d].c1 = sc.w1;
+                e[d].c2 = sc.w2;
+                e[d].c3 = sc.w3;
+                e[d].hds = sc.hds;
+                e[d].wd = (float)g->wdir[q];
+                e[d].off = sc.ay * TL_PW + sc.ax;
+                hmin = d == 0 ? sc.hds : std::min(hmin, sc.hds);
+            }
+            for (int d = 0; d < 12; ++d) e[d].hds_min = hmin;
+        }
+    g->h_wave_st.resize(t.size() * sizeof(WaveSt));
+    std::memcpy(g->h_wave_st.data(), t.data(), g->h_wave_st.size());
+    RT_CUDA(cudaMalloc(&g->d_wave_st, g->h_wave_st.size()));
+    RT_CUDA(cudaMemcpyAsync(g->d_wave_st, g->h_wave_st.data(), g->h_wave_st.size(),
+                            cudaMemcpyHostToDevice, st));
+    return RT_OK;
 }
 
 static rt_status wave_sweep(rt_grid *g, TileArgs &base, int nlam, int bc, cudaStream_t st,
@@ -396,16 +555,19 @@ static rt_status wave_sweep(rt_grid *g, TileArgs &base, int nlam, int bc, cudaSt
 {
     const char *env = std::getenv("RT_REGULAR_SWEEP");
     if (env && std::string(env) == "tile") return RT_OK;   // per-plane launches requested
-    if (g->dir_up.size() != 12 || g->dir_dn.size() != 12 || g->nz < 3 || !uniform_stencils(g))
-        return RT_OK;
+    if (g->dir_up.size() != 12 || g->dir_dn.size() != 12 || g->nz < 3) return RT_OK;
+    const bool pp = !uniform_stencils(g);
+    if (pp && !g->d_wave_st) return RT_OK;
     WaveArgs w;
+    w.st = pp ? static_cast<const WaveSt *>(g->d_wave_st) : nullptr;
     const std::vector<int> *hs[2] = {&g->dir_up, &g->dir_dn};
     for (int h = 0; h < 2; ++h) {
         TileArgs &a = w.t[h];
         a = base;
         a.ndh = 12;
         a.up = h == 0;
-        const int kref = h == 0 ? 1 : g->nz - 2;   // every plane shares this stencil
+        // uniform z: every plane shares this stencil (otherwise the table holds them)
+        const int kref = h == 0 ? 1 : g->nz - 2;
         for (int d = 0; d < 12; ++d) {
             const int q = (*hs[h])[d];
             const Stencil &sc = g->h_stencil[(size_t)kref * g->ndir + q];
@@ -417,10 +579,11 @@ static rt_status wave_sweep(rt_grid *g, TileArgs &base, int nlam, int bc, cudaSt
             a.cw[d][2] = sc.w2;
             a.cw[d][3] = sc.w3;
             a.hds[d] = sc.hds;
+            a.hds_min = d == 0 ? sc.hds : std::min(a.hds_min, sc.hds);
         }
         w.nd[h] = 12;
     }
-    const size_t plane = (size_t)nlam * 12 * g->nx * g->ny;
+    const size_t plane = (size_t)nlam * base.ntiles * 12 * TL_W * TL_H;
     const size_t nflags = 2 * (size_t)g->nz * nlam * base.ntiles;
     void *p;
     RT_TRY(scratch_get(g, 3, regular_wave_scratch(g, nlam), &p));
@@ -433,19 +596,18 @@ static rt_status wave_sweep(rt_grid *g, TileArgs &base, int nlam, int bc, cudaSt
     w.done = w.queue + 32;
     w.bc = bc;
     w.first_hemi = 0;
-    RT_CUDA(cudaMemsetAsync(w.queue, 0, (nflags + 32) * sizeof(int), st));
     const int ph = TL_H + 2 * base.hy, tsz = TL_PW * ph;
-    const size_t smem = (12 * (size_t)tsz) * sizeof(float) + (size_t)tsz * sizeof(float2);
-    RT_CUDA(cudaFuncSetAttribute(sc_wave_kernel<12>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem));
+    const size_t smem = (12 * (size_t)tsz) * sizeof(float) + (size_t)tsz * sizeof(float4);
+    void (*kern)(WaveArgs) = pp ? sc_wave_kernel<12, true> : sc_wave_kernel<12, false>;
+    RT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0, dev = 0, nsm = 0;
     RT_CUDA(cudaGetDevice(&dev));
     RT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    RT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sc_wave_kernel<12>, TL_THREADS,
-                                                          smem));
+    RT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TL_THREADS, smem));
     if (per_sm < 1) return RT_OK;
+    RT_CUDA(cudaMemsetAsync(w.queue, 0, (nflags + 32) * sizeof(int), st));
     note_launch();
-    sc_wave_kernel<12><<<per_sm * nsm, TL_THREADS, smem, st>>>(w);
+    kern<<<per_sm * nsm, TL_THREADS, smem, st>>>(w);
     RT_CUDA(cudaGetLastError());
     *done = true;
     return RT_OK;

@@ -109,6 +109,8 @@ struct rt_grid {
     rt::StencilD *d_stencil_oned = nullptr;    // FP64 copy for the adjoint
     std::vector<rt::StencilD> h_stencil_oned;
     double one_dir[3] = {0, 0, 0};
+    void *d_wave_st = nullptr;                 // [nz][2][12] per-plane stencils of the wavefront sweep
+    std::vector<char> h_wave_st;
     // voronoi
     std::vector<double> xyz;
     double box[6];
@@ -143,6 +145,8 @@ rt_status regular_cluster_sweep(rt_grid *g, int nlam, const float *alpha, const 
 rt_status regular_tile_sweep(rt_grid *g, int nlam, const float *alpha, const float *S, int bc,
                              float *J, float *buf0, float *buf1, cudaStream_t st, bool *done);
 size_t regular_wave_scratch(const rt_grid *g, int nlam);
+// builds and uploads the wavefront sweep's per-plane stencil table (no-op where it cannot apply)
+rt_status regular_wave_prepare(rt_grid *g, cudaStream_t st);
 rt_status regular_emergent(rt_grid *g, const double *dir, int nlam, const float *alpha,
                            const float *S, int bc, float *I_top, cudaStream_t st);
 size_t regular_adjoint_ws(rt_grid *g, int nlam, int stride);
