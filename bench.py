@@ -310,21 +310,33 @@ def run_gpu(args):
         torch.distributed.destroy_process_group()
 
 
+_CPU_INPUTS = {}
+
+
+def _cpu_inputs():
+    """The oracle's FP64 inputs of the benchmark workload (LTE populations), built once."""
+    if not _CPU_INPUTS:
+        from oracle.physics import Atom
+        from synth import make_atmosphere, model_atom, s4_quadrature
+        from synth.atmosphere import regular_fields
+        atm = make_atmosphere(0)
+        f, (x, y, z, dx, dy) = regular_fields(NX, NY, NZ, atm)
+        data = model_atom(np.min(f["ne"] / np.sqrt(f["T"])))
+        A = Atom(data, atm.kappa0)
+        pops = A.lte_pops(f["T"], f["ne"], f["nH"])
+        alpha, S = A.alpha_S(f["T"], f["rho"], f["ne"], pops)
+        dirs, w = s4_quadrature()
+        _CPU_INPUTS.update(alpha=alpha, S=S, dx=dx, dy=dy, z=z, dirs=dirs, w=w)
+    return _CPU_INPUTS
+
+
 def cpu_baseline(nl):
     """The oracle as it stands on this host's cores: the formal solution (sweep + J) of nl of the
     52 wavelengths on the same 128^3 grid, which is the dominant cost of the step."""
     import oracle
-    from oracle.physics import Atom
-    from synth import make_atmosphere, model_atom, s4_quadrature
-    from synth.atmosphere import regular_fields
-    atm = make_atmosphere(0)
-    f, (x, y, z, dx, dy) = regular_fields(NX, NY, NZ, atm)
-    data = model_atom(np.min(f["ne"] / np.sqrt(f["T"])))
-    A = Atom(data, atm.kappa0)
-    pops = A.lte_pops(f["T"], f["ne"], f["nH"])
-    alpha, S = A.alpha_S(f["T"], f["rho"], f["ne"], pops)
+    c = _cpu_inputs()
+    alpha, S, dx, dy, z, dirs, w = (c[k] for k in ("alpha", "S", "dx", "dy", "z", "dirs", "w"))
     pick = np.linspace(0, alpha.shape[0] - 1, nl).astype(int)
-    dirs, w = s4_quadrature()
     t = time.perf_counter()
     oracle.sc_regular(NX, NY, NZ, dx, dy, z, dirs, w, alpha[pick], S[pick])
     dt = time.perf_counter() - t
