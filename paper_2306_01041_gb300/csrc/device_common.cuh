@@ -5,6 +5,23 @@
 
 namespace rt {
 
+// e^-d from the hardware base-2 exponential, e^-d = 2^(-d log2 e); flushes results below the
+// smallest normal float (d > 87) to zero.  Relative error about 2^-22 (PTX ex2.approx).
+__device__ __forceinline__ float exp_neg(float d)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(d * -1.4426950408889634f));
+    return y;
+}
+
+// 1/x from the hardware reciprocal (PTX rcp.approx, about 1 ulp; x must be a normal float).
+__device__ __forceinline__ float rcp_fast(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Linear-S integration over one optical-depth interval d (Sect. 2.5: S linear across the
 // interval; Eq. 2):  I = I_up e^-d + w0 S_up + w1 S with e0 = 1 - e^-d, w1 = (d - e0) / d,
 // w0 = e0 - w1.  Below d = 0.1 both weights come from their Taylor series (truncated after d^5,
@@ -13,7 +30,7 @@ namespace rt {
 // (e0 >= 0.095 there, so e0 = 1 - e^-d keeps full relative precision).
 __device__ __forceinline__ void lin_weights(float d, float &ex, float &w0, float &w1)
 {
-    ex = __expf(-d);
+    ex = exp_neg(d);
     if (d < 0.1f) {   // neighbouring points have similar dtau: the branch is warp-uniform
         w1 = d * (0.5f + d * (-1.0f / 6.0f + d * (1.0f / 24.0f +
                                                 d * (-1.0f / 120.0f + d * (1.0f / 720.0f)))));
@@ -21,7 +38,7 @@ __device__ __forceinline__ void lin_weights(float d, float &ex, float &w0, float
                                                 d * (-1.0f / 30.0f + d * (1.0f / 144.0f)))));
     } else {
         const float e0 = 1.0f - ex;
-        w1 = 1.0f - e0 * __fdividef(1.0f, d);
+        w1 = 1.0f - e0 * rcp_fast(d);
         w0 = e0 - w1;
     }
 }

@@ -1,20 +1,25 @@
-// Regular grid, per-plane sweep with shared-memory tiles (same arithmetic as sc_plane_kernel).
+// Regular grid sweeps with shared-memory tiles (same arithmetic as sc_plane_kernel).
 //
-// One launch per plane step, as in sc_plane_kernel, with the upwind planes of all directions in
-// the L2-resident ping-pong buffer.  A block takes (tile, wavelength) items: it copies the tile of
+// The unit of work is a (plane step, wavelength, 32 x 32 tile) item.  A block copies the tile of
 // the upwind plane of every direction of the hemisphere, with a halo wide enough for the largest
-// stencil offset, and the interleaved (S, alpha) of the upwind plane into shared memory (16-byte
-// loads; rows wrap periodically), then computes every point of the tile for every direction from
-// shared memory.  Within a plane the stencil of a direction is a constant offset, so each corner
-// read is a fixed displacement from the point's own slot: no wrap arithmetic per update.  A thread
-// owns four points of the tile (independent dependency chains) and loops over the directions,
-// accumulating J in registers in a fixed order.  With the direction count known at compile time
-// (12 per hemisphere for the S4 set) the direction loop is unrolled and every per-direction
-// constant (offset, bilinear weights, half path length, quadrature weight) is an operand from the
-// kernel's constant bank.
+// stencil offset, and (S, alpha) of the upwind plane as pairs for x and x + 1, into shared memory
+// (16-byte loads; rows wrap periodically), then computes every point of the tile for every
+// direction from shared memory.  Within a plane the stencil of a direction is a constant offset,
+// so each corner read is a fixed displacement from the point's own slot: no wrap arithmetic per
+// update.  A thread owns two vertically adjacent points (their corner rows overlap) and loops
+// over the directions, accumulating J in registers in a fixed order.  With the direction count
+// known at compile time (12 per hemisphere for the S4 set) the direction loop is unrolled and
+// every per-direction constant (offset, bilinear weights, half path length, quadrature weight) is
+// an operand from the kernel's constant bank.
+//
+// Three schedules of the same items: sc_wave_kernel (default) runs the whole formal solution as
+// one persistent launch ordered by a device counter and per-item completion flags;
+// sc_pipe_kernel (opt-in) is that schedule with the next item's staging in flight during the
+// current one; sc_tile_kernel launches once per plane step.
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
+#include <type_traits>
 #include <string>
 
 #include "device_common.cuh"
@@ -25,7 +30,8 @@ namespace rt {
 constexpr int TL_W = 32;          // tile width (x)
 constexpr int TL_THREADS = 512;
 constexpr int TL_ROWS = TL_THREADS / TL_W;   // rows covered by one pass of the block (16)
-constexpr int TL_PPT = 2;         // points per thread (rows y and y + 16)
+constexpr int TL_PPT = 2;         // points per thread (tile rows 2 ly and 2 ly + 1)
+static_assert(TL_PPT == 2, "tile_updates shares corner rows between exactly two points");
 constexpr int TL_H = TL_ROWS * TL_PPT;       // tile height (y)
 constexpr int TL_HXP = 4;         // x halo, padded to 4 floats for 16-byte staging
 constexpr int TL_PW = TL_W + 2 * TL_HXP;
@@ -80,9 +86,9 @@ static_assert(sizeof(WaveSt) == 32, "WaveSt is two float4");
 // Interval weights for d >= 0.1 only: the same arithmetic as the d >= 0.1 branch of lin_weights.
 __device__ __forceinline__ void lin_weights_thick(float d, float &ex, float &w0, float &w1)
 {
-    ex = __expf(-d);
+    ex = exp_neg(d);
     const float e0 = 1.0f - ex;
-    w1 = 1.0f - e0 * __fdividef(1.0f, d);
+    w1 = 1.0f - e0 * rcp_fast(d);
     w0 = e0 - w1;
 }
 
@@ -111,11 +117,17 @@ __device__ __forceinline__ void tile_updates(const TileArgs &a, const WaveSt *st
             hds = a.hds[d], wd = a.w[d], off = a.off[d];
         }
         const float *Id = It + d * tsz;
+        // the thread's two points are vertically adjacent: their corner rows overlap, so three
+        // rows of intensity corners and (S, alpha) pairs serve both
+        const int o = slot[0] + off;
+        const float ic[3][2] = {{Id[o], Id[o + 1]},
+                                {Id[o + TL_PW], Id[o + TL_PW + 1]},
+                                {Id[o + 2 * TL_PW], Id[o + 2 * TL_PW + 1]}};
+        const float4 pc[3] = {SA[o], SA[o + TL_PW], SA[o + 2 * TL_PW]};   // (S, alpha) at x, x + 1
 #pragma unroll
         for (int m = 0; m < TL_PPT; ++m) {
-            const int o = slot[m] + off;
-            const float iu = c0 * Id[o] + c1 * Id[o + 1] + c2 * Id[o + TL_PW] + c3 * Id[o + TL_PW + 1];
-            const float4 p0 = SA[o], p1 = SA[o + TL_PW];   // (S, alpha) at x and x + 1
+            const float iu = c0 * ic[m][0] + c1 * ic[m][1] + c2 * ic[m + 1][0] + c3 * ic[m + 1][1];
+            const float4 p0 = pc[m], p1 = pc[m + 1];
             const float su = c0 * p0.x + c1 * p0.z + c2 * p1.x + c3 * p1.z;
             const float au = c0 * p0.y + c1 * p0.w + c2 * p1.y + c3 * p1.w;
             const float dt = (au + ak[m]) * hds;
@@ -138,13 +150,14 @@ __device__ __forceinline__ void tile_updates(const TileArgs &a, const WaveSt *st
 // which the non-coherent read-only path could serve stale) and its tile-major intensity ring
 // [nlam][ntiles][ndh][TL_H][TL_W]; otherwise the ring is [nlam][ndh][nx * ny].  PP: the plane's
 // stencils come from the table gst (copied to the shared sts), else from the arguments.
-template <int NDH, bool WAVE, bool PP>
+template <int NDH, bool WAVE, bool PP, int HY = 0>
 __device__ __forceinline__ void tile_item(const TileArgs &a, const PlaneCtx &c, int l, int tile,
                                           int x0, int y0, float *smt, const WaveSt *gst,
                                           WaveSt *sts)
 {
     const int ndh = NDH > 0 ? NDH : a.ndh;
-    const int ph = TL_H + 2 * a.hy;
+    const int hy = HY > 0 ? HY : a.hy;                       // compile-time where HY > 0
+    const int ph = TL_H + 2 * hy;
     const int tsz = TL_PW * ph;                              // slots per staged tile
     float *It = smt;                                         // [ndh][ph][TL_PW]
     float4 *SA = reinterpret_cast<float4 *>(smt + (size_t)ndh * tsz);   // [ph][TL_PW]
@@ -163,7 +176,7 @@ __device__ __forceinline__ void tile_item(const TileArgs &a, const PlaneCtx &c, 
     float amin = __int_as_float(0x7f800000);
     for (int e = tid; e < ph * q4; e += TL_THREADS) {
         const int r = e / q4, c4 = e % q4;
-        const int gy = wrapi(y0 - a.hy + r, a.ny, a.wrap1);
+        const int gy = wrapi(y0 - hy + r, a.ny, a.wrap1);
         const int gx = wrapi(x0 - TL_HXP + 4 * c4, a.nx, a.wrap1);
         const int gx4 = wrapi(gx + 4, a.nx, true);
         const size_t g = (size_t)gy * a.nx + gx;
@@ -206,11 +219,11 @@ __device__ __forceinline__ void tile_item(const TileArgs &a, const PlaneCtx &c, 
     float Sk[TL_PPT], ak[TL_PPT], jacc[TL_PPT];
     bool ok[TL_PPT];
 #pragma unroll
-    for (int m = 0; m < TL_PPT; ++m) {
-        const int x = x0 + lx, y = y0 + ly + TL_ROWS * m;
+    for (int m = 0; m < TL_PPT; ++m) {   // rows 2 ly and 2 ly + 1 of the tile
+        const int x = x0 + lx, y = y0 + TL_PPT * ly + m;
         ok[m] = x < a.nx && y < a.ny;
         gxy[m] = ok[m] ? y * a.nx + x : 0;
-        slot[m] = (ly + TL_ROWS * m + a.hy) * TL_PW + lx + TL_HXP;
+        slot[m] = (TL_PPT * ly + m + hy) * TL_PW + lx + TL_HXP;
         Sk[m] = ok[m] ? __ldg(Sl + (size_t)c.k * a.np + gxy[m]) : 0.f;
         ak[m] = ok[m] ? __ldg(al + (size_t)c.k * a.np + gxy[m]) : 0.f;
         jacc[m] = 0.f;
@@ -218,13 +231,13 @@ __device__ __forceinline__ void tile_item(const TileArgs &a, const PlaneCtx &c, 
     float *In;
     size_t dstride, mstride;
     if (WAVE) {
-        In = c.Inext + ((size_t)l * a.ntiles + tile) * ndh * (TL_W * TL_H) + ly * TL_W + lx;
+        In = c.Inext + ((size_t)l * a.ntiles + tile) * ndh * (TL_W * TL_H) + TL_PPT * ly * TL_W + lx;
         dstride = TL_W * TL_H;
-        mstride = TL_ROWS * TL_W;
+        mstride = TL_W;
     } else {
         In = c.Inext + (size_t)l * ndh * a.np + gxy[0];
         dstride = a.np;
-        mstride = (size_t)TL_ROWS * a.nx;
+        mstride = (size_t)a.nx;
     }
     if (thick)
         tile_updates<NDH, WAVE, true, PP>(a, sts, It, SA, tsz, slot, Sk, ak, ok, In, dstride,
@@ -340,7 +353,9 @@ __device__ __forceinline__ WaveItem wave_decode(const TileArgs &a, int item)
 }
 
 // PP: per-plane stencils from the table (non-uniform z); else the constant-bank stencils.
-template <int NDH, bool PP>
+// HY > 0: the stencil reach in rows, fixed at compile time (shared-memory offsets become
+// immediates); 0: from the arguments.
+template <int NDH, bool PP, int HY>
 __global__ void __launch_bounds__(TL_THREADS, 2) sc_wave_kernel(WaveArgs w)
 {
     extern __shared__ __align__(16) float smt[];
@@ -351,9 +366,9 @@ __global__ void __launch_bounds__(TL_THREADS, 2) sc_wave_kernel(WaveArgs w)
     const int total = 2 * nz * nl * nt;
     const int tx = a.tiles_x, ty = nt / a.tiles_x;
     if (threadIdx.x == 0) cur = wave_decode(a, atomicAdd(w.queue, 1));
+    __syncthreads();
     for (;;) {
-        __syncthreads();   // cur is published; the previous item is finished by every thread
-        const WaveItem it = cur;
+        const WaveItem it = cur;   // published by the barrier that ended the previous item
         if (it.item >= total) return;
         int next = 0;
         if (threadIdx.x == 0) next = atomicAdd(w.queue, 1);
@@ -384,21 +399,25 @@ __global__ void __launch_bounds__(TL_THREADS, 2) sc_wave_kernel(WaveArgs w)
         if (PP) {
             // one code copy for both hemispheres: the stencils and weights come from the table
             if (s == 0) boundary_item<NDH>(w.t[h], c, l, tile, it.x0, it.y0, w.bc);
-            else tile_item<NDH, true, true>(w.t[0], c, l, tile, it.x0, it.y0, smt,
-                                            w.st + ((size_t)k * 2 + h) * NDH, sts);
+            else tile_item<NDH, true, true, HY>(w.t[0], c, l, tile, it.x0, it.y0, smt,
+                                                w.st + ((size_t)k * 2 + h) * NDH, sts);
         } else if (h == 0) {
             // one inlined copy per hemisphere keeps every per-direction constant a static operand
             if (s == 0) boundary_item<NDH>(w.t[0], c, l, tile, it.x0, it.y0, w.bc);
-            else tile_item<NDH, true, false>(w.t[0], c, l, tile, it.x0, it.y0, smt, nullptr, nullptr);
+            else tile_item<NDH, true, false, HY>(w.t[0], c, l, tile, it.x0, it.y0, smt, nullptr,
+                                                 nullptr);
         } else {
             if (s == 0) boundary_item<NDH>(w.t[1], c, l, tile, it.x0, it.y0, w.bc);
-            else tile_item<NDH, true, false>(w.t[1], c, l, tile, it.x0, it.y0, smt, nullptr, nullptr);
+            else tile_item<NDH, true, false, HY>(w.t[1], c, l, tile, it.x0, it.y0, smt, nullptr,
+                                                 nullptr);
         }
+        // every thread read `cur` before the dependency barrier above, so the next item can be
+        // published now, by the barrier that also ends this one
+        if (threadIdx.x == 0) cur = wave_decode(a, next);
         __syncthreads();
         if (threadIdx.x == 0) {
             int *f = w.done + ((size_t)(h * nz + s) * nl + l) * nt + tile;
             asm volatile("st.release.gpu.global.b32 [%0], %1;" :: "l"(f), "r"(1) : "memory");
-            cur = wave_decode(a, next);
         }
     }
 }
@@ -508,12 +527,19 @@ static bool uniform_stencils(const rt_grid *g)
     return true;
 }
 
+static rt_status pipe_sweep(rt_grid *g, const WaveArgs &wv, int nlam, cudaStream_t st, bool *done);
+static bool pipe_geometry(const rt_grid *g, int hy);
+static size_t pipe_scratch(const rt_grid *g, int nlam, int hy);
+
 size_t regular_wave_scratch(const rt_grid *g, int nlam)
 {
     const size_t ntiles = (size_t)((g->nx + TL_W - 1) / TL_W) * ((g->ny + TL_H - 1) / TL_H);
     const size_t plane = (size_t)nlam * ntiles * 12 * TL_W * TL_H;   // tile-major ring slot
     const size_t nflags = 2 * (size_t)g->nz * nlam * ntiles;
-    return 4 * plane * sizeof(float) + (nflags + 64) * sizeof(int);
+    size_t bytes = 4 * plane * sizeof(float) + (nflags + 64) * sizeof(int);
+    int hy;
+    if (tile_geometry(g, hy) && pipe_geometry(g, hy)) bytes = std::max(bytes, pipe_scratch(g, nlam, hy));
+    return bytes;
 }
 
 rt_status regular_wave_prepare(rt_grid *g, cudaStream_t st)
@@ -583,6 +609,10 @@ static rt_status wave_sweep(rt_grid *g, TileArgs &base, int nlam, int bc, cudaSt
         }
         w.nd[h] = 12;
     }
+    w.bc = bc;
+    w.first_hemi = 0;
+    RT_TRY(pipe_sweep(g, w, nlam, st, done));
+    if (*done) return RT_OK;
     const size_t plane = (size_t)nlam * base.ntiles * 12 * TL_W * TL_H;
     const size_t nflags = 2 * (size_t)g->nz * nlam * base.ntiles;
     void *p;
@@ -594,11 +624,20 @@ static rt_status wave_sweep(rt_grid *g, TileArgs &base, int nlam, int bc, cudaSt
     w.ring[1][1] = f + 3 * plane;
     w.queue = (int *)(f + 4 * plane);
     w.done = w.queue + 32;
-    w.bc = bc;
-    w.first_hemi = 0;
     const int ph = TL_H + 2 * base.hy, tsz = TL_PW * ph;
     const size_t smem = (12 * (size_t)tsz) * sizeof(float) + (size_t)tsz * sizeof(float4);
-    void (*kern)(WaveArgs) = pp ? sc_wave_kernel<12, true> : sc_wave_kernel<12, false>;
+    void (*kern)(WaveArgs);
+    switch (base.hy * 2 + (pp ? 1 : 0)) {
+    case 2: kern = sc_wave_kernel<12, false, 1>; break;
+    case 3: kern = sc_wave_kernel<12, true, 1>; break;
+    case 4: kern = sc_wave_kernel<12, false, 2>; break;
+    case 5: kern = sc_wave_kernel<12, true, 2>; break;
+    case 6: kern = sc_wave_kernel<12, false, 3>; break;
+    case 7: kern = sc_wave_kernel<12, true, 3>; break;
+    case 8: kern = sc_wave_kernel<12, false, 4>; break;
+    case 9: kern = sc_wave_kernel<12, true, 4>; break;
+    default: kern = pp ? sc_wave_kernel<12, true, 0> : sc_wave_kernel<12, false, 0>; break;
+    }
     RT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0, dev = 0, nsm = 0;
     RT_CUDA(cudaGetDevice(&dev));
@@ -609,6 +648,497 @@ static rt_status wave_sweep(rt_grid *g, TileArgs &base, int nlam, int bc, cudaSt
     note_launch();
     kern<<<per_sm * nsm, TL_THREADS, smem, st>>>(w);
     RT_CUDA(cudaGetLastError());
+    *done = true;
+    return RT_OK;
+}
+
+// ---- Pipelined persistent sweep ------------------------------------------------------------------
+//
+// The wavefront schedule of sc_wave_kernel with the staging of the next item overlapped with the
+// computation of the current one.  One block of 512 threads per SM holds two staging buffers.
+// The intensity ring is tile major with each tile's halo stored beside it,
+// [nlam][tile][12][PH][TL_PW], so the 12 upwind planes an item needs are one contiguous block:
+// a single cp.async.bulk (the TMA engine, completion counted on an mbarrier) brings it into
+// shared memory.  S and alpha of the upwind plane (caller's arrays, periodic wrap) arrive by
+// 16-byte cp.async and are interleaved into (S, alpha) pairs for x and x + 1 after landing.
+// Writers store each point into its own tile's region and, near a tile edge, into the halo of
+// the neighbouring tile(s).  Applies to planes whose sides are multiples of 32 (at least 64) and
+// stencils within HY <= 4 rows.
+//
+// Ordering: an item's intensities are requested only once its 3 x 3 neighbours of the previous
+// step are complete.  The request for the next item is attempted (without waiting) while the
+// current one is computed; if the neighbours are not complete yet, it is made after the current
+// item is published.  A block only ever waits for items that precede, in counter order, every
+// item it holds, so by induction on the smallest unfinished item the waits cannot deadlock.
+// All waits are bounded (ERR_TIMEOUT).
+constexpr int PL_THREADS = 512;
+
+struct PipeArgs {
+    TileArgs t[2];             // per hemisphere (uniform z: the stencils as in sc_wave_kernel)
+    const WaveSt *st;          // [nz][2][12] per-plane stencils (non-uniform z), else null
+    float *ring[2][2];         // [hemisphere][step parity] padded tile-major planes
+    int *queue;
+    int *done;                 // [2][nz][nlam][ntiles] completion flags
+    int bc, first_hemi;
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *m, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(m)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait for phase `parity` of an mbarrier to complete
+__device__ __forceinline__ bool mbar_wait(uint64_t *m, uint32_t parity)
+{
+    for (int it = 0; it < (1 << 20); ++it)
+        if (mbar_try_wait(m, parity)) return true;
+    return false;
+}
+
+// one thread: announce `bytes` on the mbarrier and start the bulk copy global -> shared
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *m)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 :: "r"(smem_addr(m)), "r"(bytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        :: "r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(m)) : "memory");
+}
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(smem_addr(dst)), "l"(src)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
+
+// flag index of item (h, s, l, tile)
+__device__ __forceinline__ size_t flag_at(const TileArgs &a, int h, int s, int l, int tile)
+{
+    return ((size_t)(h * a.nz + s) * a.nlam + l) * a.ntiles + tile;
+}
+
+// lanes 0..8 of one warp: the 3 x 3 neighbour flags of item `it` at its previous step.
+// blocking = false: one look; true: bounded wait.  Returns the warp-wide "all complete".
+__device__ __forceinline__ bool deps_ready(const PipeArgs &w, const WaveItem &it, bool blocking)
+{
+    const TileArgs &a = w.t[0];
+    const int lane = threadIdx.x & 31;
+    bool ok = true;
+    if (lane < 9) {
+        const int tx = a.tiles_x, ty = a.ntiles / a.tiles_x;
+        const int tx0 = it.tile % tx, ty0 = it.tile / tx;
+        const int nx_ = (tx0 + lane % 3 - 1 + tx) % tx, ny_ = (ty0 + lane / 3 - 1 + ty) % ty;
+        const int *f = w.done + flag_at(a, it.h, it.s - 1, it.l, ny_ * tx + nx_);
+        if (blocking) {
+            ok = wait_flag(f, a.err);
+        } else {
+            int v;
+            asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
+            ok = v != 0;
+        }
+    }
+    return __all_sync(0xffffffffu, ok);
+}
+
+// S and alpha of item `it`'s upwind plane into raw[0] (S) and raw[TSZ] (alpha), and of its own
+// points into own[0] and own[TL_W * TL_H]: 16-byte copies
+template <int HY>
+__device__ __forceinline__ void stage_sa_async(const TileArgs &a, const WaveItem &it, float *raw,
+                                               float *own)
+{
+    constexpr int PH = TL_H + 2 * HY, TSZ = PH * TL_PW, Q4 = TL_PW / 4;
+    const bool up = it.h == 0;
+    const int k = up ? it.s : a.nz - 1 - it.s;
+    const int ku = up ? k - 1 : k + 1;
+    const size_t npt = (size_t)a.np * a.nz;
+    const float *Sl = a.S + (size_t)it.l * npt, *Al = a.alpha + (size_t)it.l * npt;
+    const float *Su = Sl + (size_t)ku * a.np, *Au = Al + (size_t)ku * a.np;
+    for (int e = threadIdx.x; e < PH * Q4; e += PL_THREADS) {
+        const int r = e / Q4, c4 = e % Q4;
+        const int gy = wrapi(it.y0 - HY + r, a.ny, true);
+        const int gx = wrapi(it.x0 - TL_HXP + 4 * c4, a.nx, true);
+        const size_t g = (size_t)gy * a.nx + gx;
+        cp_async16(raw + r * TL_PW + 4 * c4, Su + g);
+        cp_async16(raw + TSZ + r * TL_PW + 4 * c4, Au + g);
+    }
+    if (threadIdx.x < TL_H * TL_W / 4) {
+        const int r = threadIdx.x / (TL_W / 4), c4 = threadIdx.x % (TL_W / 4);
+        const size_t g = (size_t)k * a.np + (size_t)(it.y0 + r) * a.nx + it.x0 + 4 * c4;
+        cp_async16(own + r * TL_W + 4 * c4, Sl + g);
+        cp_async16(own + TL_W * TL_H + r * TL_W + 4 * c4, Al + g);
+    }
+}
+
+// where a thread's point (row yl of the tile, column lx) is stored in the padded ring, as offsets
+// from the ring slot's wavelength base: its own tile's region and, near a tile edge, the halo of
+// the neighbouring tile(s); -1 where there is no such copy
+template <int HY>
+struct RingDst {
+    int own, xc, yc, cc;
+};
+
+template <int HY>
+__device__ __forceinline__ RingDst<HY> ring_dst(const TileArgs &a, int tile, int lx, int yl)
+{
+    constexpr int PH = TL_H + 2 * HY, TSZ = PH * TL_PW, REG = 12 * TSZ;
+    const int tx = a.tiles_x, ty = a.ntiles / a.tiles_x;
+    const int tx0 = tile % tx, ty0 = tile / tx;
+    RingDst<HY> r;
+    r.own = tile * REG + (yl + HY) * TL_PW + lx + TL_HXP;
+    int ntx = -1, col = 0, nty = -1, row = 0;
+    if (lx < TL_HXP) ntx = (tx0 + tx - 1) % tx, col = lx + TL_W + TL_HXP;
+    else if (lx >= TL_W - TL_HXP) ntx = (tx0 + 1) % tx, col = lx - (TL_W - TL_HXP);
+    if (yl < HY) nty = (ty0 + ty - 1) % ty, row = yl + TL_H + HY;
+    else if (yl >= TL_H - HY) nty = (ty0 + 1) % ty, row = yl - (TL_H - HY);
+    r.xc = ntx >= 0 ? (ty0 * tx + ntx) * REG + (yl + HY) * TL_PW + col : -1;
+    r.yc = nty >= 0 ? (nty * tx + tx0) * REG + row * TL_PW + lx + TL_HXP : -1;
+    r.cc = (ntx >= 0 && nty >= 0) ? (nty * tx + ntx) * REG + row * TL_PW + col : -1;
+    return r;
+}
+
+template <int HY>
+__device__ __forceinline__ void ring_store(float *base, const RingDst<HY> &r, int d, float v)
+{
+    constexpr int TSZ = (TL_H + 2 * HY) * TL_PW;
+    __stcg(base + r.own + d * TSZ, v);
+    if (r.xc >= 0) __stcg(base + r.xc + d * TSZ, v);
+    if (r.yc >= 0) {
+        __stcg(base + r.yc + d * TSZ, v);
+        if (r.cc >= 0) __stcg(base + r.cc + d * TSZ, v);
+    }
+}
+
+template <int HY, bool PP>
+__global__ void __launch_bounds__(PL_THREADS, 1) sc_pipe_kernel(PipeArgs w)
+{
+    constexpr int PH = TL_H + 2 * HY, TSZ = PH * TL_PW, REG = 12 * TSZ, NP = TL_W * TL_H;
+    extern __shared__ __align__(128) float smp[];
+    float *It = smp;                                             // [2][12][TSZ]
+    float *raw = smp + 2 * REG;                                  // [2][2][TSZ] upwind (S, alpha)
+    float *own = raw + 4 * TSZ;                                  // [2][2][NP] own plane (S, alpha)
+    float4 *SA = reinterpret_cast<float4 *>(own + 4 * NP);       // [TSZ]
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ WaveItem cur_s, nxt_s;
+    __shared__ int pf_s[2];   // [b]: the next item's intensities were requested during item b
+    __shared__ __align__(16) WaveSt sts[PP ? 12 : 1];
+    const TileArgs &a0 = w.t[0];
+    const int nt = a0.ntiles, nl = a0.nlam, nz = a0.nz;
+    const int total = 2 * nz * nl * nt;
+    const int tid = threadIdx.x, lx = tid % TL_W, ly = tid / TL_W;
+    const size_t npt = (size_t)a0.np * nz;
+
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&mbar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&mbar[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        cur_s = wave_decode(a0, atomicAdd(w.queue, 1));
+        nxt_s = wave_decode(a0, atomicAdd(w.queue, 1));
+        pf_s[0] = pf_s[1] = 0;
+    }
+    __syncthreads();
+    uint32_t phase0 = 0, phase1 = 0;
+    int b = 0;
+    {
+        // the first item: wait for its neighbours (nothing else is held), then request it
+        const WaveItem c0 = cur_s;
+        if (c0.item >= total) return;
+        if (c0.s > 0) {
+            if (tid < 32) {
+                const bool ok = deps_ready(w, c0, true);
+                if (tid == 0) {
+                    if (!ok) flag_error(a0.err, ERR_TIMEOUT);
+                    asm volatile("fence.proxy.async.global;" ::: "memory");
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    bulk_load(It, w.ring[c0.h][(c0.s + 1) & 1] + ((size_t)c0.l * nt + c0.tile) * REG,
+                              REG * sizeof(float), &mbar[0]);
+                }
+            }
+            stage_sa_async<HY>(a0, c0, raw, own);
+        }
+        cp_async_commit();
+    }
+    for (;;) {
+        // cur_s and nxt_s were written before the barrier that ended the previous item
+        const WaveItem cur = cur_s, nxt = nxt_s;
+        if (cur.item >= total) break;
+        int claim = 0;
+        if (tid == 0) {
+            claim = atomicAdd(w.queue, 1);
+            pf_s[b] = 0;
+        }
+        const bool nxt_valid = nxt.item < total;
+        float *It_c = It + b * REG, *raw_c = raw + b * 2 * TSZ, *own_c = own + b * 2 * NP;
+        float *It_n = It + (b ^ 1) * REG;
+        // 1. S and alpha of the next item (inputs: no dependency)
+        if (nxt_valid && nxt.s > 0) stage_sa_async<HY>(a0, nxt, raw + (b ^ 1) * 2 * TSZ,
+                                                       own + (b ^ 1) * 2 * NP);
+        cp_async_commit();
+        // 2. the current item's staged data
+        bool lost = false;
+        if (cur.s > 0) {
+            lost = !mbar_wait(&mbar[b], b ? phase1 : phase0);
+            if (b) phase1 ^= 1u;
+            else phase0 ^= 1u;
+        }
+        cp_async_wait<1>();
+        if (__syncthreads_or(lost)) {
+            // the bulk copy did not complete: record it, give any copy still in flight a bounded
+            // time to land, and leave
+            if (tid == 0) {
+                flag_error(a0.err, ERR_TIMEOUT);
+                if (pf_s[b ^ 1]) mbar_wait(&mbar[b ^ 1], b ? phase0 : phase1);
+            }
+            cp_async_wait<0>();
+            return;
+        }
+        const bool up = cur.h == 0;
+        const int k = up ? cur.s : nz - 1 - cur.s;
+        const TileArgs &a = w.t[cur.h];
+        // 3. the consumed ring region is dead: drop it from L2 without a write-back; (S, alpha)
+        //    pairs; the thick-item vote; per-plane stencils; the J dependency; an attempt to
+        //    request the next item's intensities
+        float amin = __int_as_float(0x7f800000);
+        if (cur.s > 0) {
+            {   // REG floats = REG / 32 lines of 128 bytes (the region starts on a line)
+                const float *src = w.ring[cur.h][(cur.s + 1) & 1] + ((size_t)cur.l * nt + cur.tile) * REG;
+                for (int q = tid; q < REG / 32; q += PL_THREADS)
+                    asm volatile("discard.global.L2 [%0], 128;" :: "l"(src + q * 32) : "memory");
+            }
+            for (int e = tid; e < TSZ; e += PL_THREADS) {
+                const int c = e % TL_PW;
+                const float s0 = raw_c[e], a0v = raw_c[TSZ + e];
+                const float s1 = c + 1 < TL_PW ? raw_c[e + 1] : s0;
+                const float a1 = c + 1 < TL_PW ? raw_c[TSZ + e + 1] : a0v;
+                SA[e] = make_float4(s0, a0v, s1, a1);
+                amin = fminf(amin, a0v);
+            }
+            if (PP && tid < 12 * 8)
+                reinterpret_cast<int *>(sts)[tid] = __ldg(
+                    reinterpret_cast<const int *>(w.st + ((size_t)k * 2 + cur.h) * 12) + tid);
+        }
+        const bool first = cur.h == w.first_hemi;
+        if (tid < 32) {
+            if (!first) {   // the upward J of this plane and tile is complete
+                bool ok = true;
+                if (tid == 0) ok = wait_flag(w.done + flag_at(a0, 0, k, cur.l, cur.tile), a0.err);
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (tid == 0 && !ok) flag_error(a0.err, ERR_TIMEOUT);
+            }
+            if (nxt_valid && nxt.s > 0 && deps_ready(w, nxt, false)) {
+                if (tid == 0) {
+                    asm volatile("fence.proxy.async.global;" ::: "memory");
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    bulk_load(It_n, w.ring[nxt.h][(nxt.s + 1) & 1] +
+                                        ((size_t)nxt.l * nt + nxt.tile) * REG,
+                              REG * sizeof(float), &mbar[b ^ 1]);
+                    pf_s[b] = 1;
+                }
+            }
+        }
+        const float hds_min = PP ? (cur.s > 0 ? __ldg(&w.st[((size_t)k * 2 + cur.h) * 12].hds_min) : 0.f)
+                                 : a.hds_min;
+        const bool thick = __syncthreads_and(cur.s > 0 && amin * hds_min >= 0.1f * 1.0001f);
+        // 4. the item
+        float *ringn = w.ring[cur.h][cur.s & 1] + (size_t)cur.l * nt * REG;
+        float jacc[TL_PPT], jold[TL_PPT];
+        int gxy[TL_PPT];
+        RingDst<HY> dst[TL_PPT];
+#pragma unroll
+        for (int m = 0; m < TL_PPT; ++m) {
+            const int yl = ly + TL_ROWS * m;
+            gxy[m] = (cur.y0 + yl) * a0.nx + cur.x0 + lx;
+            dst[m] = ring_dst<HY>(a0, cur.tile, lx, yl);
+            jacc[m] = 0.f;
+            jold[m] = first ? 0.f : __ldcg(a0.J + (size_t)cur.l * npt + (size_t)k * a0.np + gxy[m]);
+        }
+        if (cur.s == 0) {
+            const float *Sl = a0.S + (size_t)cur.l * npt + (size_t)k * a0.np;
+#pragma unroll
+            for (int m = 0; m < TL_PPT; ++m) {
+                const float Sk = __ldg(Sl + gxy[m]);
+                const float v = (w.bc == RT_BC_THERMAL && up) ? Sk : 0.f;
+#pragma unroll
+                for (int d = 0; d < 12; ++d) {
+                    ring_store<HY>(ringn, dst[m], d, v);
+                    jacc[m] += a.w[d] * v;
+                }
+            }
+        } else {
+            float Sk[TL_PPT], ak[TL_PPT];
+            int slot[TL_PPT];
+#pragma unroll
+            for (int m = 0; m < TL_PPT; ++m) {
+                const int q = (ly + TL_ROWS * m) * TL_W + lx;
+                Sk[m] = own_c[q];
+                ak[m] = own_c[NP + q];
+                slot[m] = (ly + TL_ROWS * m + HY) * TL_PW + lx + TL_HXP;
+            }
+            auto body = [&](auto thick_tag) {
+                constexpr bool THICK = decltype(thick_tag)::value;
+#pragma unroll
+                for (int d = 0; d < 12; ++d) {
+                    float c0, c1, c2, c3, hds, wd;
+                    int off;
+                    if (PP) {
+                        const float4 q0 = reinterpret_cast<const float4 *>(sts)[2 * d];
+                        const float4 q1 = reinterpret_cast<const float4 *>(sts)[2 * d + 1];
+                        c0 = q0.x, c1 = q0.y, c2 = q0.z, c3 = q0.w;
+                        hds = q1.x, wd = q1.y, off = __float_as_int(q1.z);
+                    } else {
+                        c0 = a.cw[d][0], c1 = a.cw[d][1], c2 = a.cw[d][2], c3 = a.cw[d][3];
+                        hds = a.hds[d], wd = a.w[d], off = a.off[d];
+                    }
+                    const float *Id = It_c + d * TSZ;
+#pragma unroll
+                    for (int m = 0; m < TL_PPT; ++m) {
+                        const int o = slot[m] + off;
+                        const float iu = c0 * Id[o] + c1 * Id[o + 1] + c2 * Id[o + TL_PW] +
+                                         c3 * Id[o + TL_PW + 1];
+                        const float4 p0 = SA[o], p1 = SA[o + TL_PW];
+                        const float su = c0 * p0.x + c1 * p0.z + c2 * p1.x + c3 * p1.z;
+                        const float au = c0 * p0.y + c1 * p0.w + c2 * p1.y + c3 * p1.w;
+                        const float dt = (au + ak[m]) * hds;
+                        float ex, w0, w1;
+                        if (THICK) lin_weights_thick(dt, ex, w0, w1);
+                        else lin_weights(dt, ex, w0, w1);
+                        const float v = iu * ex + w0 * su + w1 * Sk[m];
+                        ring_store<HY>(ringn, dst[m], d, v);
+                        jacc[m] += wd * v;
+                    }
+                }
+            };
+            if (thick) body(std::true_type{});
+            else body(std::false_type{});
+        }
+#pragma unroll
+        for (int m = 0; m < TL_PPT; ++m) {
+            float *Jp = a0.J + (size_t)cur.l * npt + (size_t)k * a0.np + gxy[m];
+            const float v = first ? jacc[m] : jold[m] + jacc[m];
+            if (!isfinite(v)) flag_error(a0.err, ERR_NAN);
+            __stcg(Jp, v);
+        }
+        // the ring stores are read next by the bulk copies (async proxy) of other blocks
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        if (tid == 0) {   // every thread read cur_s and nxt_s before the first barrier of the item
+            cur_s = nxt;
+            nxt_s = wave_decode(a0, claim);
+        }
+        __syncthreads();
+        // 5. publish the item; request the next one now if the attempt above found it not ready
+        if (tid == 0) {
+            int *f = w.done + flag_at(a0, cur.h, cur.s, cur.l, cur.tile);
+            asm volatile("st.release.gpu.global.b32 [%0], %1;" :: "l"(f), "r"(1) : "memory");
+        }
+        if (tid < 32 && !pf_s[b] && nxt_valid && nxt.s > 0) {
+            const bool ok = deps_ready(w, nxt, true);
+            if (tid == 0) {
+                if (!ok) flag_error(a0.err, ERR_TIMEOUT);
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                bulk_load(It_n, w.ring[nxt.h][(nxt.s + 1) & 1] + ((size_t)nxt.l * nt + nxt.tile) * REG,
+                          REG * sizeof(float), &mbar[b ^ 1]);
+            }
+        }
+        b ^= 1;
+    }
+    cp_async_wait<0>();
+}
+
+// Scratch of the pipelined sweep: 4 padded ring slots, flags, counter.
+static size_t pipe_scratch(const rt_grid *g, int nlam, int hy)
+{
+    const size_t ntiles = (size_t)(g->nx / TL_W) * (g->ny / TL_H);
+    const size_t slot = (size_t)nlam * ntiles * 12 * (TL_H + 2 * hy) * TL_PW;
+    const size_t nflags = 2 * (size_t)g->nz * nlam * ntiles;
+    return 4 * slot * sizeof(float) + (nflags + 64) * sizeof(int);
+}
+
+static bool pipe_geometry(const rt_grid *g, int hy)
+{
+    return g->nx % TL_W == 0 && g->ny % TL_H == 0 && g->nx >= 2 * TL_W && g->ny >= 2 * TL_H &&
+           hy >= 1 && hy <= 4;
+}
+
+static bool pipe_applies(const rt_grid *g, int hy)
+{
+    const char *env = std::getenv("RT_REGULAR_SWEEP");   // opt-in: RT_REGULAR_SWEEP=pipe
+    return env && std::string(env) == "pipe" && pipe_geometry(g, hy);
+}
+
+template <int HY, bool PP>
+static rt_status launch_pipe(PipeArgs &w, cudaStream_t st)
+{
+    constexpr int PH = TL_H + 2 * HY, TSZ = PH * TL_PW;
+    const size_t smem = (size_t)(2 * 12 * TSZ + 4 * TSZ + 4 * TL_W * TL_H) * sizeof(float) +
+                        (size_t)TSZ * sizeof(float4);
+    RT_CUDA(cudaFuncSetAttribute(sc_pipe_kernel<HY, PP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+    int per_sm = 0, dev = 0, nsm = 0;
+    RT_CUDA(cudaGetDevice(&dev));
+    RT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    RT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sc_pipe_kernel<HY, PP>, PL_THREADS,
+                                                          smem));
+    if (per_sm < 1) return fail(RT_ECAPACITY, "pipelined sweep cannot be resident");
+    note_launch();
+    sc_pipe_kernel<HY, PP><<<per_sm * nsm, PL_THREADS, smem, st>>>(w);
+    RT_CUDA(cudaGetLastError());
+    return RT_OK;
+}
+
+static rt_status pipe_sweep(rt_grid *g, const WaveArgs &wv, int nlam, cudaStream_t st, bool *done)
+{
+    const int hy = wv.t[0].hy;
+    if (!pipe_applies(g, hy)) return RT_OK;
+    const bool pp = wv.st != nullptr;
+    PipeArgs w;
+    w.t[0] = wv.t[0];
+    w.t[1] = wv.t[1];
+    w.st = wv.st;
+    w.bc = wv.bc;
+    w.first_hemi = wv.first_hemi;
+    const size_t ntiles = (size_t)wv.t[0].ntiles;
+    const size_t slot = (size_t)nlam * ntiles * 12 * (TL_H + 2 * hy) * TL_PW;
+    const size_t nflags = 2 * (size_t)g->nz * nlam * ntiles;
+    void *p;
+    RT_TRY(scratch_get(g, 3, pipe_scratch(g, nlam, hy), &p));
+    float *f = (float *)p;
+    w.ring[0][0] = f;
+    w.ring[0][1] = f + slot;
+    w.ring[1][0] = f + 2 * slot;
+    w.ring[1][1] = f + 3 * slot;
+    w.queue = (int *)(f + 4 * slot);
+    w.done = w.queue + 32;
+    RT_CUDA(cudaMemsetAsync(w.queue, 0, (nflags + 32) * sizeof(int), st));
+    rt_status r;
+    switch (hy * 2 + (pp ? 1 : 0)) {
+    case 2: r = launch_pipe<1, false>(w, st); break;
+    case 3: r = launch_pipe<1, true>(w, st); break;
+    case 4: r = launch_pipe<2, false>(w, st); break;
+    case 5: r = launch_pipe<2, true>(w, st); break;
+    case 6: r = launch_pipe<3, false>(w, st); break;
+    case 7: r = launch_pipe<3, true>(w, st); break;
+    case 8: r = launch_pipe<4, false>(w, st); break;
+    default: r = launch_pipe<4, true>(w, st); break;
+    }
+    RT_TRY(r);
     *done = true;
     return RT_OK;
 }

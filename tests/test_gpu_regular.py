@@ -127,14 +127,17 @@ def test_full_size_128cubed_sampled_wavelengths(rt):
                                               ((64, 64, 40), 4, "uniform"), ((36, 48, 17), 3, "uniform"),
                                               ((16, 16, 5), 2, "uniform"), ((96, 40, 33), 5, "uniform"),
                                               ((64, 64, 40), 4, "stretched"),
-                                              ((36, 40, 19), 3, "stretched")])
+                                              ((36, 40, 19), 3, "stretched"),
+                                              ((128, 64, 33), 3, "stretched"),
+                                              ((64, 96, 20), 2, "uniform")])
 def test_sweep_variants_match_each_other_and_oracle(rt, monkeypatch, shape, nlam, zkind):
-    """The regular-grid sweeps -- the persistent wavefront kernel (default wherever the staged tile
-    covers every stencil: constant-bank stencils on uniform z, per-plane stencil tables on
-    stretched z), shared-memory tiles per plane, thread-block clusters holding whole planes, and
-    the plain per-plane kernel -- compute the same updates: each matches the oracle and the
-    others (up to FMA contraction).  "rough" z steps reach beyond the tile halo, where the
-    default falls back to the plain kernel."""
+    """The regular-grid sweeps -- the persistent wavefront kernel (default wherever the staged
+    tile covers every stencil; constant-bank stencils on uniform z, per-plane stencil tables on
+    stretched z), its pipelined variant with bulk-copied staging (opt-in; plane sides multiples
+    of 32), shared-memory tiles per plane, thread-block clusters holding whole planes, and the
+    plain per-plane kernel -- compute the same updates: each matches the oracle and the others
+    (up to FMA contraction).  "rough" z steps reach beyond the tile halo, where the default falls
+    back to the plain kernel."""
     import torch
     nx, ny, nz = shape
     rng = np.random.default_rng(21)
@@ -151,8 +154,8 @@ def test_sweep_variants_match_each_other_and_oracle(rt, monkeypatch, shape, nlam
     g = rt.RegularGrid(nx, ny, nz, 0.7, 0.9, z, dirs, w)
     Jr = oracle.sc_regular(nx, ny, nz, 0.7, 0.9, z, dirs, w, a, s)
     out = {}
-    for mode in ("wave", "tile", "cluster", "plane"):
-        if mode == "wave":
+    for mode in ("default", "pipe", "tile", "cluster", "plane"):
+        if mode == "default":
             monkeypatch.delenv("RT_REGULAR_SWEEP", raising=False)
         else:
             monkeypatch.setenv("RT_REGULAR_SWEEP", mode)
@@ -161,10 +164,14 @@ def test_sweep_variants_match_each_other_and_oracle(rt, monkeypatch, shape, nlam
         J = rt.formal_solution(g, ag, sg)
         launched = rt.kernel_launches() - n0
         torch.cuda.synchronize()
-        if mode == "wave" and zkind != "rough":
+        if mode == "default" and zkind != "rough":
             assert launched == 1, launched   # one persistent launch for both hemispheres
+        if mode == "pipe" and zkind != "rough" and nx % 32 == 0 and ny % 32 == 0 and \
+                min(nx, ny) >= 64:
+            assert launched == 1, launched
         out[mode] = J.cpu().numpy().astype(np.float64)
         assert_parity(out[mode], Jr, what=f"{mode} J")
-    assert_parity(out["wave"], out["plane"], rel=2e-6, what="wave vs plane")
+    assert_parity(out["default"], out["plane"], rel=2e-6, what="default vs plane")
+    assert_parity(out["pipe"], out["plane"], rel=2e-6, what="pipe vs plane")
     assert_parity(out["tile"], out["plane"], rel=2e-6, what="tile vs plane")
     assert_parity(out["cluster"], out["plane"], rel=2e-6, what="cluster vs plane")
