@@ -377,16 +377,20 @@ def _make_vor(args):
     s, n = args
     sys.path.insert(0, ROOT)
     from synth import make_atmosphere, make_voronoi_grid
-    atm = make_atmosphere(s)
-    g = make_voronoi_grid(atm, n, "rho03" if s % 2 else "dtau", s)
+    atm = make_atmosphere(s if s <= 8 else 0)
+    g = make_voronoi_grid(atm, n, "rho03" if (s <= 8 and s % 2) else "dtau", s)
     f = atm.fields(g["xyz"][:, 0], g["xyz"][:, 1], g["xyz"][:, 2])
     return s, g, f, atm.kappa0
 
 
-def voronoi_workload(sizes=VOR_SIZES):
+def voronoi_workload(sizes=VOR_SIZES, extra=((9, 200000), (10, 20000))):
+    """The 8 batched atmospheres (seeds 1-8), plus the 200k-site adjoint grid and the 20k-site LTE
+    continuum grid (site seeds 9 and 10, atmosphere seed 0, density from |dtau/dz|), built in
+    parallel."""
     import multiprocessing as mp
-    with mp.get_context("spawn").Pool(min(len(sizes), os.cpu_count() or 1)) as pool:
-        return pool.map(_make_vor, list(zip(range(1, len(sizes) + 1), sizes)))
+    jobs = list(zip(range(1, len(sizes) + 1), sizes)) + list(extra)
+    with mp.get_context("spawn").Pool(min(len(jobs), os.cpu_count() or 1)) as pool:
+        return pool.map(_make_vor, jobs)
 
 
 def run_extras(torch, rt, dev):
@@ -399,6 +403,8 @@ def run_extras(torch, rt, dev):
     work = voronoi_workload()
     out["voronoi_grid_build_s"] = round(time.perf_counter() - t0, 1)
     dirs, w = s4_quadrature()
+    extra = {s: (g, f, kappa0) for s, g, f, kappa0 in work if s > 8}
+    work = [x for x in work if x[0] <= 8]
     grids, atoms, atmoss, alphas, Ss = [], [], [], [], []
     for s, g, f, kappa0 in work:
         G = rt.VoronoiGrid(g["xyz"], g["nbr_off"], g["nbr_idx"], g["nbr_shift"], g["box"], dirs, w)
@@ -428,8 +434,13 @@ def run_extras(torch, rt, dev):
         return e0.elapsed_time(e1) / reps
 
     Jp = [torch.empty_like(a) for a in alphas]
+    os.environ["RT_VORONOI_SWEEP"] = "levels"      # plain per-direction, per-level launches
     ms_plain = timeit(lambda: [rt.formal_solution(g, a, sv, J=j)
                                for g, a, sv, j in zip(grids, alphas, Ss, Jp)])
+    del os.environ["RT_VORONOI_SWEEP"]
+    Js = [torch.empty_like(a) for a in alphas]      # one persistent launch per grid, in turn
+    ms_single = timeit(lambda: [rt.formal_solution(g, a, sv, J=j)
+                                for g, a, sv, j in zip(grids, alphas, Ss, Js)])
     from paper_2306_01041_gb300.autotune import tune_batch
     batch, choice = tune_batch(grids, alphas, Ss, nlam)
     Jb = [torch.empty_like(a) for a in alphas]
@@ -439,7 +450,9 @@ def run_extras(torch, rt, dev):
         "atmospheres": len(grids), "sites": [g.npt for g in grids],
         "levels_max": [g.max_levels for g in grids], "wavelengths": nlam, "directions": NDIR,
         "plain_ms": round(ms_plain, 2), "batched_ms": round(ms_batch, 2),
+        "per_grid_persistent_ms": round(ms_single, 2),
         "plain_gupd_s": round(upd / ms_plain / 1e6, 3),
+        "per_grid_persistent_gupd_s": round(upd / ms_single / 1e6, 3),
         "batched_gupd_s": round(upd / ms_batch / 1e6, 3),
         "speedup": round(ms_plain / ms_batch, 2), "max_rel_diff_batched_vs_plain": diff,
         "autotuned": choice}
@@ -475,7 +488,69 @@ def run_extras(torch, rt, dev):
     # time to convergence: the 128^3 regular grid and the 215k-site irregular grid
     out["convergence"] = convergence_times(torch, rt, dev, grids[5], atoms[5], atmoss[5])
     out["adjoint"] = adjoint_timing(torch, rt, dev)
+    out["adjoint_voronoi_200k"] = voronoi_adjoint_timing(torch, rt, dev, *extra[9], dirs, w)
+    out["lte_continuum"] = lte_continuum_timing(torch, rt, dev, *extra[10], dirs, w)
     return out
+
+
+def _events(torch, fn, reps=3):
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def voronoi_adjoint_timing(torch, rt, dev, g, f, kappa0, dirs, w):
+    """Emergent mu = 1 intensity and its adjoint at the line core and both continua on the
+    200k-site grid, populations at LTE."""
+    from synth import model_atom
+    G = rt.VoronoiGrid(g["xyz"], g["nbr_off"], g["nbr_idx"], g["nbr_shift"], g["box"], dirs, w)
+    data = model_atom(np.min(f["ne"] / np.sqrt(f["T"])))
+    A = rt.Atom(data, kappa0)
+    M = rt.Atmos(*[torch.tensor(f[k], dtype=torch.float32, device=dev)
+                   for k in ("T", "rho", "ne", "nH")])
+    pops = rt.lte_populations(G, A, M)
+    a, sv = rt.source_terms(G, A, M, pops)
+    core = int(np.argmin(np.abs(np.asarray(data["lam"]) - data["lam0"])))
+    pick = [core, len(data["lam"]) - 2, len(data["lam"]) - 1]
+    a3, s3 = a[pick].contiguous(), sv[pick].contiguous()
+    gI = torch.ones((3, G.ntop), device=dev)
+    res = {"sites": G.npt, "top_sites": G.ntop,
+           "emergent_ms": round(_events(torch, lambda: rt.emergent_intensity(
+               G, (0.0, 0.0, 1.0), a3, s3)), 3)}
+    for stride in (1, 8):
+        res[f"adjoint_stride_{stride}_ms"] = round(_events(torch, lambda: rt.formal_solution_adjoint(
+            G, (0.0, 0.0, 1.0), a3, s3, gI, ckpt_stride=stride)), 3)
+        res[f"adjoint_stride_{stride}_workspace_MB"] = round(
+            rt.lib().rt_adjoint_workspace_size(G.handle, 3, stride) / 2 ** 20, 1)
+    return res
+
+
+def lte_continuum_timing(torch, rt, dev, g, f, kappa0, dirs, w):
+    """The small LTE continuum workloads (500 nm, 24 directions): 32x32x64 regular and the
+    20k-site Voronoi grid; latency-bound (64 planes, or tens of levels per direction)."""
+    from synth import make_atmosphere
+    from synth.atmosphere import regular_fields
+    res = {}
+    atm = make_atmosphere(0)
+    fr, (x, y, z, dx, dy) = regular_fields(32, 32, 64, atm)
+    gr = rt.RegularGrid(32, 32, 64, dx, dy, z, dirs, w)
+    G = rt.VoronoiGrid(g["xyz"], g["nbr_off"], g["nbr_idx"], g["nbr_shift"], g["box"], dirs, w)
+    for name, grid, ff in (("regular_32x32x64", gr, fr), ("voronoi_20k", G, f)):
+        al, S = rt.source_terms_lte(torch.tensor(ff["T"], dtype=torch.float32, device=dev),
+                                    torch.tensor(ff["rho"], dtype=torch.float32, device=dev),
+                                    atm.kappa0, 500e-9)
+        al, S = al[None].contiguous(), S[None].contiguous()
+        J = torch.empty_like(al)
+        ms = _events(torch, lambda: rt.formal_solution(grid, al, S, J=J), reps=10)
+        res[name] = {"formal_solution_ms": round(ms, 4),
+                     "gupd_s": round(grid.npt * NDIR / ms / 1e6, 3)}
+    return res
 
 
 def convergence_times(torch, rt, dev, vgrid, vatom, vatm):

@@ -43,7 +43,61 @@ struct BatchArgs {
     int nitems, ndir, nlam, bc;
 };
 
-__global__ void __launch_bounds__(512) batch_sweep_kernel(const BatchArgs a)
+// One (site, wavelength) update of a level, split into its loads (gather) and its arithmetic, so
+// that a thread can have the loads of one update in flight with the table loads of the next.
+struct VorGather {
+    float Si, Ai, I1, S1, A1, I2, S2, A2;
+};
+
+__device__ __forceinline__ VorGather vor_gather(const BatchGridDev &g, const float *I, const Upwind &u,
+                                                int i, int l, int nlam, float inflow_scale)
+{
+    VorGather r;
+    const size_t il = (size_t)i * nlam + l;
+    r.Si = __ldg(g.S + il);
+    r.Ai = __ldg(g.A + il);
+    // a wall neighbour (k < 0) takes the site's own S and alpha; -1 (inflow wall of the sweep)
+    // brings the boundary intensity S * inflow_scale (1 thermal, 0 otherwise), -2 zero
+    if (u.k1 >= 0) {
+        const size_t kl = (size_t)u.k1 * nlam + l;
+        r.I1 = I[kl];
+        r.S1 = __ldg(g.S + kl);
+        r.A1 = __ldg(g.A + kl);
+    } else {
+        r.S1 = r.Si;
+        r.A1 = r.Ai;
+        r.I1 = u.k1 == -1 ? r.Si * inflow_scale : 0.f;
+    }
+    if (u.k2 >= 0 && u.w1 != 1.f) {
+        const size_t kl = (size_t)u.k2 * nlam + l;
+        r.I2 = I[kl];
+        r.S2 = __ldg(g.S + kl);
+        r.A2 = __ldg(g.A + kl);
+    } else {
+        r.S2 = r.Si;
+        r.A2 = r.Ai;
+        r.I2 = u.k2 == -1 ? r.Si * inflow_scale : 0.f;
+    }
+    return r;
+}
+
+__device__ __forceinline__ float vor_update(const Upwind &u, const VorGather &r)
+{
+    float acc = 0.f;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const float wk = c ? 1.f - u.w1 : u.w1;
+        if (wk == 0.f) continue;
+        const float len = c ? u.l2 : u.l1;
+        const float Ik = c ? r.I2 : r.I1, Sk = c ? r.S2 : r.S1, Ak = c ? r.A2 : r.A1;
+        float ex, w0, w1;
+        lin_weights(0.5f * (Ak + r.Ai) * len, ex, w0, w1);
+        acc += wk * (Ik * ex + w0 * Sk + w1 * r.Si);
+    }
+    return acc;
+}
+
+__global__ void __launch_bounds__(512, 2) batch_sweep_kernel(const BatchArgs a)
 {
     __shared__ int item_s;
     for (;;) {
@@ -59,40 +113,35 @@ __global__ void __launch_bounds__(512) batch_sweep_kernel(const BatchArgs a)
         const int32_t *order = g.order + (size_t)d * g.n;
         float *I = g.I + (size_t)d * g.n * a.nlam;
         const int b0 = g.lvl_base[d], b1 = g.lvl_base[d + 1];
-        const bool upd = a.up_flag[d] > 0.f;
+        const float inflow = (a.bc == RT_BC_THERMAL && a.up_flag[d] > 0.f) ? 1.f : 0.f;
+        const int lc = item.lc;
+        const int64_t B = blockDim.x;
         for (int L = b0; L + 1 < b1; ++L) {
             const int64_t s0 = g.lvl[L], s1 = g.lvl[L + 1];
-            const int64_t work = (s1 - s0) * item.lc;
-            for (int64_t t = threadIdx.x; t < work; t += blockDim.x) {
-                const int64_t slot = s0 + t / item.lc;
-                const int l = item.c0 + (int)(t % item.lc);
-                const Upwind u = up[slot];
-                const int i = order[slot];
-                const size_t il = (size_t)i * a.nlam + l;
-                const float Si = __ldg(g.S + il), Ai = __ldg(g.A + il);
-                float acc = 0.f;
-#pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    const int k = c ? u.k2 : u.k1;
-                    const float wk = c ? 1.f - u.w1 : u.w1;
-                    const float len = c ? u.l2 : u.l1;
-                    if (wk == 0.f) continue;
-                    float Ik, Sk, Ak;
-                    if (k >= 0) {
-                        const size_t kl = (size_t)k * a.nlam + l;
-                        Ik = I[kl];
-                        Sk = __ldg(g.S + kl);
-                        Ak = __ldg(g.A + kl);
-                    } else {
-                        Sk = Si;
-                        Ak = Ai;
-                        Ik = (a.bc == RT_BC_THERMAL && upd && k == -1) ? Si : 0.f;
-                    }
-                    float ex, w0, w1;
-                    lin_weights(0.5f * (Ak + Ai) * len, ex, w0, w1);
-                    acc += wk * (Ik * ex + w0 * Sk + w1 * Si);
-                }
-                I[il] = acc;
+            const int64_t work = (s1 - s0) * lc;
+            // the tables (upwind record, site) of a thread's next update are loaded before the
+            // gathers of the current one: two independent load streams in flight per thread
+            auto table = [&](int64_t t, Upwind &uu, int &ii, int &ll) {
+                const int64_t slot = s0 + t / lc;
+                ll = item.c0 + (int)(t % lc);
+                uu = up[slot];
+                ii = order[slot];
+            };
+            int64_t t = threadIdx.x;
+            Upwind u;
+            int i = 0, l = 0;
+            if (t < work) table(t, u, i, l);
+            while (t < work) {
+                const int64_t tn = t + B;
+                Upwind un;
+                int in = 0, ln = 0;
+                if (tn < work) table(tn, un, in, ln);
+                const VorGather gr = vor_gather(g, I, u, i, l, a.nlam, inflow);
+                I[(size_t)i * a.nlam + l] = vor_update(u, gr);
+                t = tn;
+                u = un;
+                i = in;
+                l = ln;
             }
             __syncthreads();
         }
@@ -153,6 +202,7 @@ struct rt_batch {
     float *d_fields = nullptr;   // per grid A, S, J [n][nlam] and I [ndir][n][nlam]
     int *d_queue = nullptr;
     unsigned *d_err = nullptr;
+    unsigned *err = nullptr;     // where kernels flag errors: d_err, or the grid's for a batch of one
     ~rt_batch()
     {
         cudaFree(d_items);
@@ -290,6 +340,7 @@ rt_status rt_batch_create(const rt_grid_t *grids, int ngrids, int nlam, const in
     BT(cudaMemcpy(b->d_wdir, wd.data(), b->ndir * sizeof(float), cudaMemcpyHostToDevice));
     BT(cudaMemcpy(b->d_upf, uf.data(), b->ndir * sizeof(float), cudaMemcpyHostToDevice));
     BT(cudaMemset(b->d_err, 0, sizeof(unsigned)));
+    b->err = ngrids == 1 ? grids[0]->d_err : b->d_err;
 #undef BT
     if (e != cudaSuccess) {
         delete b;
@@ -321,7 +372,7 @@ rt_status rt_batch_formal_solution(rt_batch_t b, const float *const *alpha, cons
     a.queue = b->d_queue;
     a.wdir = b->d_wdir;
     a.up_flag = b->d_upf;
-    a.err = b->d_err;
+    a.err = b->err;
     a.nitems = (int)b->h_items.size();
     a.ndir = b->ndir;
     a.nlam = b->nlam;
@@ -334,7 +385,7 @@ rt_status rt_batch_formal_solution(rt_batch_t b, const float *const *alpha, cons
         const size_t m = (size_t)g.n * b->nlam;
         note_launch();
         batch_reduce_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(g.I, g.J, b->d_wdir,
-                                                                         b->ndir, m, b->d_err);
+                                                                         b->ndir, m, b->err);
         transpose_b(g.J, J[i], g.n, b->nlam, st);
     }
     RT_CUDA(cudaGetLastError());

@@ -644,8 +644,10 @@ rt_status rt_lambda_iterate(rt_grid_t g, const rt_atom *atom, const rt_atmos *at
             RT_TRY(scratch_get(g, 0, 2 * (size_t)nlam * ndh * g->nx * g->ny * sizeof(float), &q));
             RT_TRY(scratch_get(g, 3, regular_wave_scratch(g, nlam), &q));
         }
-        else
+        else {
             RT_TRY(scratch_get(g, 0, 4 * (size_t)n * nlam * sizeof(float), &q));
+            RT_TRY(voronoi_prepare(g, nlam));
+        }
         RT_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         RT_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
         RT_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));

@@ -121,6 +121,8 @@ struct rt_grid {
     std::vector<int8_t> nbr_shift;
     rt::VorTables vt;                          // the quadrature directions
     rt::VorTables vt_one;                      // cache: one extra direction (emergent/adjoint)
+    rt_batch *self_batch = nullptr;            // persistent all-direction sweep of this grid alone
+    int self_batch_nlam = 0;
     int64_t n_fallback = 0;
     int max_levels = 0;
     std::vector<int64_t> top;                  // emergent-layer points
@@ -145,6 +147,9 @@ rt_status regular_cluster_sweep(rt_grid *g, int nlam, const float *alpha, const 
 rt_status regular_tile_sweep(rt_grid *g, int nlam, const float *alpha, const float *S, int bc,
                              float *J, float *buf0, float *buf1, cudaStream_t st, bool *done);
 size_t regular_wave_scratch(const rt_grid *g, int nlam);
+// Voronoi: builds what the formal solution of nlam wavelengths allocates on first use (call
+// outside stream capture)
+rt_status voronoi_prepare(rt_grid *g, int nlam);
 // builds and uploads the wavefront sweep's per-plane stencil table (no-op where it cannot apply)
 rt_status regular_wave_prepare(rt_grid *g, cudaStream_t st);
 rt_status regular_emergent(rt_grid *g, const double *dir, int nlam, const float *alpha,

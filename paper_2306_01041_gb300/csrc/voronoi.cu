@@ -7,6 +7,8 @@
 // (site, wavelength) of the current level.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
+#include <string>
 
 #include "device_common.cuh"
 #include "rt_impl.h"
@@ -133,10 +135,43 @@ static void sweep_direction(const rt_grid *g, const VorTables &vt, int d, VorArg
     }
 }
 
+// The persistent all-direction sweep (the batched kernel on this grid alone) applies to the
+// plain formal solution: J only, thermal or zero inflow.  RT_VORONOI_SWEEP=levels selects the
+// per-direction, per-level launches instead.
+static bool self_batch_applies(int bc, const float *I_dir)
+{
+    const char *env = std::getenv("RT_VORONOI_SWEEP");
+    if (env && std::string(env) == "levels") return false;
+    return bc != RT_BC_ARRAY && !I_dir;
+}
+
+rt_status voronoi_prepare(rt_grid *g, int nlam)
+{
+    if (!self_batch_applies(RT_BC_THERMAL, nullptr)) return RT_OK;
+    if (g->self_batch && g->self_batch_nlam == nlam) return RT_OK;
+    if (g->self_batch) rt_batch_destroy(g->self_batch);
+    g->self_batch = nullptr;
+    rt_grid_t gg = g;
+    RT_TRY(rt_batch_create(&gg, 1, nlam, nullptr, 0, &g->self_batch));
+    g->self_batch_nlam = nlam;
+    return RT_OK;
+}
+
 rt_status voronoi_formal_solution(rt_grid *g, int nlam, const float *alpha, const float *S,
                                   int bc, const float *I_bc, float *J, float *I_dir,
                                   cudaStream_t st)
 {
+    if (self_batch_applies(bc, I_dir)) {
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        RT_CUDA(cudaStreamIsCapturing(st, &cap));
+        // building the batch allocates: not while a stream is being captured
+        if (cap == cudaStreamCaptureStatusNone) RT_TRY(voronoi_prepare(g, nlam));
+        if (g->self_batch && g->self_batch_nlam == nlam) {
+            const float *al[1] = {alpha}, *Sl[1] = {S};
+            float *Jl[1] = {J};
+            return rt_batch_formal_solution(g->self_batch, al, Sl, bc, Jl, st);
+        }
+    }
     const int64_t n = g->nsites;
     const size_t f = (size_t)n * nlam;
     void *p;

@@ -91,3 +91,34 @@ def test_lte_continuum_20k_sites(rt):
                                 dirs, 7.0)
     Jr = oracle.voronoi_fs(tab, dirs, w, a[None], s[None])
     assert_parity(J.cpu().numpy(), Jr, what="J 20k")
+
+
+@pytest.mark.parametrize("bc,nlam,n", [(0, 5, 500), (1, 7, 1500), (1, 52, 800)])
+def test_persistent_sweep_equals_level_launches(rt, monkeypatch, bc, nlam, n):
+    """The default J-only formal solution runs every direction of the grid in one persistent
+    launch (per-direction intensities, J reduced in direction order); it equals the per-direction,
+    per-level launches bit for bit and matches the oracle."""
+    import torch
+    g = _small(7, n)
+    dirs, w = s4_quadrature()
+    rng = np.random.default_rng(9)
+    a = 10.0 ** rng.uniform(-4, 2, (nlam, n))
+    s = rng.uniform(0.5, 2.0, (nlam, n))
+    G = _grid(rt, g, dirs, w)
+    out = {}
+    for mode in ("persistent", "levels"):
+        if mode == "levels":
+            monkeypatch.setenv("RT_VORONOI_SWEEP", "levels")
+        else:
+            monkeypatch.delenv("RT_VORONOI_SWEEP", raising=False)
+        n0 = rt.kernel_launches()
+        out[mode] = rt.formal_solution(G, to_gpu(a), to_gpu(s), bc=bc).cpu()
+        launched = rt.kernel_launches() - n0
+        if mode == "persistent":   # transposes of alpha and S, sweep, J reduction, transpose
+            assert launched == 5, launched
+        torch.cuda.synchronize()
+    assert torch.equal(out["persistent"], out["levels"])
+    tab = oracle.voronoi_tables(g["xyz"], g["nbr_off"], g["nbr_idx"], g["nbr_shift"], g["box"],
+                                dirs, 7.0)
+    Jr = oracle.voronoi_fs(tab, dirs, w, a, s, bc=bc)
+    assert_parity(out["persistent"].numpy(), Jr, what="J persistent")
