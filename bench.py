@@ -493,6 +493,36 @@ def run_extras(torch, rt, dev):
     return out
 
 
+def run_voronoi_batch(args):
+    """The batched Voronoi formal solution alone on the first N atmospheres of the 8-atmosphere
+    workload (52 wavelengths, 24 directions, populations at LTE): a smaller case of the batched
+    kernel for profiling.  Prints one JSON line."""
+    import torch
+    import paper_2306_01041_gb300 as rt
+    from synth import model_atom, s4_quadrature
+    dev = torch.device("cuda", 0)
+    work = voronoi_workload(VOR_SIZES[:args.voronoi_batch], extra=())
+    dirs, w = s4_quadrature()
+    grids, alphas, Ss = [], [], []
+    for s, g, f, kappa0 in work:
+        G = rt.VoronoiGrid(g["xyz"], g["nbr_off"], g["nbr_idx"], g["nbr_shift"], g["box"], dirs, w)
+        A = rt.Atom(model_atom(np.min(f["ne"] / np.sqrt(f["T"]))), kappa0)
+        M = rt.Atmos(*[torch.tensor(f[k], dtype=torch.float32, device=dev)
+                       for k in ("T", "rho", "ne", "nH")])
+        a, sv = rt.source_terms(G, A, M, rt.lte_populations(G, A, M))
+        grids.append(G)
+        alphas.append(a)
+        Ss.append(sv)
+    nlam = alphas[0].shape[0]
+    batch = rt.Batch(grids, nlam)
+    Js = [torch.empty_like(a) for a in alphas]
+    ms = _events(torch, lambda: batch.formal_solution(alphas, Ss, Js=Js), reps=args.steps)
+    upd = sum(g.npt for g in grids) * NDIR * nlam
+    print(json.dumps({"workload": f"batched Voronoi formal solution, {len(grids)} atmospheres",
+                      "sites": [g.npt for g in grids], "ms": round(ms, 3),
+                      "gupd_s": round(upd / ms / 1e6, 3)}))
+
+
 def _events(torch, fn, reps=3):
     fn()
     torch.cuda.synchronize()
@@ -622,6 +652,9 @@ def main():
     ap.add_argument("--cpu-lams", type=int, default=52)
     ap.add_argument("--nx", type=int, default=128,
                     help="grid size per axis (profiling uses smaller cases; the benchmark is 128)")
+    ap.add_argument("--voronoi-batch", type=int, default=0,
+                    help="time only the batched Voronoi formal solution on the first N of the 8 "
+                         "atmospheres (a smaller case for profiling)")
     ap.add_argument("--z-stretch", type=float, default=0.0,
                     help="non-uniform z spacing amplitude a in [0, 1) (cell heights (1 -+ a) dz)")
     args = ap.parse_args()
@@ -633,6 +666,9 @@ def main():
         WORKLOAD += f", stretched z (a = {args.z_stretch})"
     if args.warmup < 3:
         args.warmup = 3
+    if args.voronoi_batch:
+        run_voronoi_batch(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

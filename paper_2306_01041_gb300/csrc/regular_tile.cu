@@ -53,6 +53,7 @@ struct TileArgs {
     float cw[TL_MAX_DH][4];   // bilinear weights
     float hds[TL_MAX_DH];
     float hds_min;            // min over the directions of hds
+    int lchunk;               // persistent sweeps: wavelengths swept together through all planes
 };
 
 __device__ __forceinline__ int wrapi(int v, int n, bool once)
@@ -334,18 +335,28 @@ struct WaveItem {
     int item, h, s, l, tile, x0, y0, pad;
 };
 
+// Item order of the persistent sweeps: hemisphere, then chunks of `lchunk` wavelengths (the last
+// may be shorter), then plane step, wavelength within the chunk, tile.  A chunk goes through all
+// planes before the next starts, which bounds the intensity ring that must stay in L2 between a
+// step and the next to lchunk x tiles items.  Every item's dependencies (previous step of the
+// same wavelength; the upward item of the same plane) come earlier in this order.
 __device__ __forceinline__ WaveItem wave_decode(const TileArgs &a, int item)
 {
-    const int nt = a.ntiles, nl = a.nlam;
-    const int per_hemi = a.nz * nl * nt;
+    const int nt = a.ntiles, nl = a.nlam, nz = a.nz, lc = a.lchunk;
+    const int per_hemi = nz * nl * nt;
     WaveItem it;
     it.item = item;
     it.h = item / per_hemi;
     int rem = item - it.h * per_hemi;
-    it.s = rem / (nl * nt);
-    rem -= it.s * (nl * nt);
-    it.l = rem / nt;
-    it.tile = rem - it.l * nt;
+    const int per_chunk = nz * lc * nt, full = nl / lc;
+    int c = rem / per_chunk;
+    if (c > full) c = full;
+    const int l0 = c * lc, lcc = c < full ? lc : nl - l0;
+    rem -= c * per_chunk;
+    it.s = rem / (lcc * nt);
+    rem -= it.s * (lcc * nt);
+    it.l = l0 + rem / nt;
+    it.tile = rem % nt;
     it.x0 = (it.tile % a.tiles_x) * TL_W;
     it.y0 = (it.tile / a.tiles_x) * TL_H;
     it.pad = 0;
@@ -611,6 +622,19 @@ static rt_status wave_sweep(rt_grid *g, TileArgs &base, int nlam, int bc, cudaSt
     }
     w.bc = bc;
     w.first_hemi = 0;
+    {
+        // wavelengths per chunk: enough items per plane step (about 1.5 per resident block at
+        // two blocks per SM) that an item's neighbours of the previous step are normally done
+        // when it is claimed, and no more, so that the intensity ring of the chunk stays in L2.
+        // RT_WAVE_LCHUNK overrides (tuning).
+        int dev = 0, nsm = 0;
+        RT_CUDA(cudaGetDevice(&dev));
+        RT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        int lc = (3 * nsm + base.ntiles - 1) / base.ntiles;
+        if (const char *e = std::getenv("RT_WAVE_LCHUNK")) lc = std::atoi(e);
+        lc = std::max(1, std::min(nlam, lc));
+        w.t[0].lchunk = w.t[1].lchunk = lc;
+    }
     RT_TRY(pipe_sweep(g, w, nlam, st, done));
     if (*done) return RT_OK;
     const size_t plane = (size_t)nlam * base.ntiles * 12 * TL_W * TL_H;
@@ -1164,6 +1188,7 @@ rt_status regular_tile_sweep(rt_grid *g, int nlam, const float *alpha, const flo
     a.tiles_x = (g->nx + TL_W - 1) / TL_W;
     a.ntiles = a.tiles_x * ((g->ny + TL_H - 1) / TL_H);
     a.wrap1 = (g->nx >= TL_PW && g->ny >= TL_H + 2 * hy) ? 1 : 0;
+    a.lchunk = nlam;
     RT_TRY(wave_sweep(g, a, nlam, bc, st, done));
     if (*done) return RT_OK;
     float *bufs[2] = {buf0, buf1};
