@@ -625,12 +625,15 @@ static rt_status wave_sweep(rt_grid *g, TileArgs &base, int nlam, int bc, cudaSt
     {
         // wavelengths per chunk: enough items per plane step (about 1.5 per resident block at
         // two blocks per SM) that an item's neighbours of the previous step are normally done
-        // when it is claimed, and no more, so that the intensity ring of the chunk stays in L2.
-        // RT_WAVE_LCHUNK overrides (tuning).
+        // when it is claimed, and no more, so that the intensity ring of the chunk stays in L2;
+        // chunks of equal size (a short last chunk starves the blocks).  At 128 x 128 and 52
+        // wavelengths: two chunks of 26.  RT_WAVE_LCHUNK overrides (tuning).
         int dev = 0, nsm = 0;
         RT_CUDA(cudaGetDevice(&dev));
         RT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-        int lc = (3 * nsm + base.ntiles - 1) / base.ntiles;
+        const int target = std::max(1, (3 * nsm + base.ntiles - 1) / base.ntiles);
+        const int nch = std::max(1, (nlam + target / 2) / target);
+        int lc = (nlam + nch - 1) / nch;
         if (const char *e = std::getenv("RT_WAVE_LCHUNK")) lc = std::atoi(e);
         lc = std::max(1, std::min(nlam, lc));
         w.t[0].lchunk = w.t[1].lchunk = lc;
