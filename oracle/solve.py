@@ -19,6 +19,11 @@ class RegularGrid:
         self.wdir = np.asarray(wdir, float)
         self.periodic = periodic
 
+    def lambda_star(self, alpha, bc=0):
+        from .ali import lambda_star_regular
+        return lambda_star_regular(self.nx, self.ny, self.nz, self.dx, self.dy, self.z, self.dirs,
+                                   self.wdir, alpha, bc=bc, periodic=self.periodic)
+
     def formal_solution(self, alpha, S, bc=0, ibc=None, want_I=False):
         return lib.sc_regular(self.nx, self.ny, self.nz, self.dx, self.dy, self.z, self.dirs,
                               self.wdir, alpha, S, bc=bc, ibc=ibc, periodic=self.periodic,
@@ -32,6 +37,10 @@ class VoronoiGrid:
         self.tab = lib.voronoi_tables(grid["xyz"], grid["nbr_off"], grid["nbr_idx"],
                                       grid["nbr_shift"], grid["box"], self.dirs, r_exp)
         self.order = lib.voronoi_order(self.tab["level"])
+
+    def lambda_star(self, alpha, bc=0):
+        from .ali import lambda_star_voronoi
+        return lambda_star_voronoi(self.tab, self.dirs, self.wdir, alpha, bc=bc)
 
     def formal_solution(self, alpha, S, bc=0, ibc=None, want_I=False):
         return lib.voronoi_fs(self.tab, self.dirs, self.wdir, alpha, S, bc=bc, ibc=ibc,
