@@ -598,13 +598,17 @@ def convergence_times(torch, rt, dev, vgrid, vatom, vatm):
                    for k in ("T", "rho", "ne", "nH")])
     for name, (G, AA, MM) in (("regular_128^3", (g, A, M)),
                               ("voronoi_%d_sites" % vgrid.npt, (vgrid, vatom, vatm[0]))):
-        pops = rt.lte_populations(G, AA, MM)
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        it, hist, conv = rt.lambda_iterate(G, AA, MM, pops, max_iter=300, tol=1e-3)
-        dt = time.perf_counter() - t
-        res[name] = {"iterations": it, "converged": bool(conv), "seconds": round(dt, 3),
-                     "s_per_iteration": round(dt / it, 5), "final_change": float(hist[-1])}
+        for method, fn in (("lambda", rt.lambda_iterate), ("ali", rt.lambda_iterate_ali)):
+            pops = rt.lte_populations(G, AA, MM)
+            fn(G, AA, MM, pops, max_iter=1, tol=1e-3)        # first-call set-up, untimed
+            pops = rt.lte_populations(G, AA, MM)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            it, hist, conv = fn(G, AA, MM, pops, max_iter=300, tol=1e-3)
+            dt = time.perf_counter() - t
+            res[f"{name}_{method}"] = {"iterations": it, "converged": bool(conv),
+                                       "seconds": round(dt, 3), "s_per_iteration": round(dt / it, 5),
+                                       "final_change": float(hist[-1])}
     return res
 
 

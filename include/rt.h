@@ -18,7 +18,8 @@
  *     Voronoi grid.  They must be 16-byte aligned, else RT_EINVAL.
  *   - The library owns the grid tables and the scratch it allocates for a grid.
  *   - Calls are asynchronous on the given CUDA stream (NULL = legacy default stream), except
- *     rt_grid_create and rt_lambda_iterate, which synchronise on their stream.
+ *     rt_grid_create, rt_lambda_iterate and rt_lambda_iterate_ali, which synchronise on their
+ *     stream.
  *   - No call aborts.  Errors come back as rt_status; rt_last_error() returns a message for the
  *     calling host thread.  Device-side failures (a non-finite value, an exhausted wait) are
  *     recorded in a device error word and surfaced by the next synchronising call.
@@ -168,6 +169,44 @@ rt_status rt_statistical_equilibrium(rt_grid_t grid, const rt_atom *atom, const 
 rt_status rt_lambda_iterate(rt_grid_t grid, const rt_atom *atom, const rt_atmos *atm,
                             float *pops, int max_iter, double tol, int *iters_out,
                             float *history, int use_graph, void *stream);
+
+/* ---- accelerated Lambda iteration ------------------------------------------------------------
+ * The paper iterates plain Lambda (Sect. 2.1) and notes that accelerated schemes need far fewer
+ * iterations.  Here each point's own contribution to its J is treated implicitly: with
+ * Lambda*_p = dJ_p/dS_p (opacities fixed), the new populations solve
+ *     n = SE( J + Lambda* (S(n) - S_old) )
+ * at every point.  At a converged state S(n) = S_old, so the fixed point is the Lambda
+ * iteration's; only the number of iterations changes. */
+
+/* Lambda* [nlam][npt] (device, overwritten) of the opacities alpha [nlam][npt]: the sum over
+ * directions of w_d times the weight with which S at a point enters its own intensity (w1 of
+ * the interval ending there, Eq. 2; 1 where a ray starts at the point under RT_BC_THERMAL; on a
+ * Voronoi grid, w0 + w1 (+ e^-d under thermal inflow) for a wall neighbour, which stands in with
+ * the site's own S).  bc: RT_BC_THERMAL, RT_BC_ZERO, or RT_BC_ARRAY (inflow independent of S,
+ * as ZERO).  The first call on a Voronoi grid uploads site-ordered tables (allocates). */
+rt_status rt_lambda_star(rt_grid_t grid, int nlam, const float *alpha, int bc, float *Lstar,
+                         void *stream);
+
+/* One accelerated statistical-equilibrium update: J, Lstar and S_old [nlam][npt] (S_old the
+ * source function of the current populations, from which J was computed); pops [3][npt] read
+ * (current) and overwritten (new); *dmax_dev (device, may be NULL) as for
+ * rt_statistical_equilibrium.  The local equation is solved by `newton` (0..16) Newton steps on
+ * the logarithms of the two smaller populations (forward-difference Jacobian); 0 gives the plain
+ * update. */
+rt_status rt_statistical_equilibrium_ali(rt_grid_t grid, const rt_atom *atom,
+                                         const rt_atmos *atm, const float *J, const float *Lstar,
+                                         const float *S_old, float *pops, float *dmax_dev,
+                                         int newton, void *stream);
+
+/* Accelerated Lambda iteration: as rt_lambda_iterate, with the update of
+ * rt_statistical_equilibrium_ali (newton steps, 0..16; 1 suffices after the first iterations).
+ * fixed_lstar != 0: Lambda* from the opacities of the starting populations, held fixed (the
+ * fixed point does not depend on Lambda*, only the rate of convergence does); 0: recomputed from
+ * every iteration's opacities.  Takes at most 64 wavelengths. */
+rt_status rt_lambda_iterate_ali(rt_grid_t grid, const rt_atom *atom, const rt_atmos *atm,
+                                float *pops, int max_iter, double tol, int *iters_out,
+                                float *history, int use_graph, int newton, int fixed_lstar,
+                                void *stream);
 
 /* ---- emergent intensity and its adjoint (Sect. 2.5-2.6; Eq. 2 differentiated) -------------- */
 /* Intensity along one direction dir[3] (mu_z > 0) at the emergent layer:

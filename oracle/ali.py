@@ -99,12 +99,15 @@ def lambda_star_voronoi(tab, dirs, wdir, alpha, bc=0):
 
 
 def _local_update(atom, T, rho, ne, nH, pops, J, Lst, S_old, newton):
-    """n = SE(J + Lambda* (S(n) - S_old)) at every point, by Newton's method from ``pops``."""
+    """n = SE(J + Lambda* (S(n) - S_old)) at every point, by ``newton`` Newton steps from
+    ``pops`` (0: the plain update SE(J))."""
     def G(n):
         _, S = atom.alpha_S(T, rho, ne, n)
         P = atom.rate_matrix(T, ne, J + Lst * (S - S_old))
         return atom.statistical_equilibrium(P, nH)
 
+    if newton == 0:            # the plain update
+        return G(pops)
     npt = nH.size
     idx = np.arange(npt)
     big = np.argmax(pops, axis=0)
@@ -143,16 +146,20 @@ def _local_update(atom, T, rho, ne, nH, pops, J, Lst, S_old, newton):
     return full(x)
 
 
-def ali_iterate(grid, atom, T, rho, ne, nH, pops0=None, max_iter=300, tol=1e-3, newton=3):
-    """Accelerated Lambda iteration.  ``grid`` is an ``oracle.solve`` grid.  Returns (pops,
-    iterations, history of the largest relative population change)."""
+def ali_iterate(grid, atom, T, rho, ne, nH, pops0=None, max_iter=300, tol=1e-3, newton=3,
+                fixed_lstar=False):
+    """Accelerated Lambda iteration.  ``grid`` is an ``oracle.solve`` grid.  ``fixed_lstar``:
+    Lambda* of the starting populations' opacities held fixed (the fixed point does not depend
+    on it).  Returns (pops, iterations, history of the largest relative population change)."""
     pops = atom.lte_pops(T, ne, nH) if pops0 is None else np.array(pops0, float)
     hist = []
     it = 0
+    Lst = None
     for it in range(1, max_iter + 1):
         alpha, S = atom.alpha_S(T, rho, ne, pops)
         J = grid.formal_solution(alpha, S, bc=0)
-        Lst = grid.lambda_star(alpha, bc=0)
+        if Lst is None or not fixed_lstar:
+            Lst = grid.lambda_star(alpha, bc=0)
         new = _local_update(atom, T, rho, ne, nH, pops, J, Lst, S, newton)
         dmax = float(np.max(np.abs(new - pops) / new))
         hist.append(dmax)

@@ -7,5 +7,6 @@ Build the library first (``python -c "import __graft_entry__ as g; g.build()"`` 
 from ._lib import (RT_BC_ARRAY, RT_BC_THERMAL, RT_BC_ZERO, RTError, lib)  # noqa: F401
 from .api import (Atmos, Atom, Batch, EmergentIntensity, Grid, RegularGrid,  # noqa: F401
                   VoronoiGrid, emergent_intensity, formal_solution, formal_solution_adjoint,
-                  kernel_launches, lambda_iterate, lte_populations, source_terms, source_terms_adjoint,
-                  source_terms_lte, source_terms_lte_adjoint, statistical_equilibrium)
+                  kernel_launches, lambda_iterate, lambda_iterate_ali, lambda_star,
+                  lte_populations, source_terms, source_terms_adjoint, source_terms_lte,
+                  source_terms_lte_adjoint, statistical_equilibrium, statistical_equilibrium_ali)

@@ -73,6 +73,13 @@ SIGNATURES = {
                                            ctypes.POINTER(AtmosDesc), P, P, P, P]),
     "rt_lambda_iterate": (c_int, [P, ctypes.POINTER(AtomDesc), ctypes.POINTER(AtmosDesc), P, c_int,
                                   c_double, ctypes.POINTER(c_int), PF, c_int, P]),
+    "rt_lambda_star": (c_int, [P, c_int, P, c_int, P, P]),
+    "rt_statistical_equilibrium_ali": (c_int, [P, ctypes.POINTER(AtomDesc),
+                                               ctypes.POINTER(AtmosDesc), P, P, P, P, P, c_int,
+                                               P]),
+    "rt_lambda_iterate_ali": (c_int, [P, ctypes.POINTER(AtomDesc), ctypes.POINTER(AtmosDesc), P,
+                                      c_int, c_double, ctypes.POINTER(c_int), PF, c_int, c_int,
+                                      c_int, P]),
     "rt_emergent_intensity": (c_int, [P, PD, c_int, P, P, c_int, P, P]),
     "rt_adjoint_workspace_size": (c_size_t, [P, c_int, c_int]),
     "rt_formal_solution_adjoint": (c_int, [P, PD, c_int, P, P, c_int, P, P, P, c_int, P, c_size_t,

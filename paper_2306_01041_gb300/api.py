@@ -255,6 +255,43 @@ def lambda_iterate(grid, atom: Atom, atm: Atmos, pops, max_iter=300, tol=1e-3, u
     return it.value, hist[:it.value].copy(), st == L.RT_OK
 
 
+def lambda_star(grid, alpha, bc=L.RT_BC_THERMAL, out=None, stream=None):
+    """Lambda* [nlam][npt]: dJ_p/dS_p at fixed opacities (the diagonal of the Lambda operator)."""
+    nlam = alpha.shape[0]
+    Ls = torch.empty_like(alpha) if out is None else out
+    check(lib().rt_lambda_star(grid.handle, nlam, _dev(alpha, (nlam, grid.npt), "alpha"), int(bc),
+                               _dev(Ls, (nlam, grid.npt), "Lstar"), _stream(stream)))
+    return Ls
+
+
+def statistical_equilibrium_ali(grid, atom: Atom, atm: Atmos, J, Lstar, S_old, pops, newton=3,
+                                stream=None):
+    """Accelerated update of pops in place (see rt_statistical_equilibrium_ali); returns the
+    device scalar max |dn/n|."""
+    dmax = torch.zeros(1, device="cuda", dtype=torch.float32)
+    check(lib().rt_statistical_equilibrium_ali(grid.handle, ctypes.byref(atom.desc),
+                                               ctypes.byref(atm.desc), _dev(J), _dev(Lstar),
+                                               _dev(S_old), _dev(pops), _dev(dmax), int(newton),
+                                               _stream(stream)))
+    return dmax
+
+
+def lambda_iterate_ali(grid, atom: Atom, atm: Atmos, pops, max_iter=300, tol=1e-3,
+                       use_graph=True, newton=1, fixed_lstar=True, stream=None):
+    """Accelerated Lambda iteration in place on pops; returns (iterations, history, converged).
+    ``fixed_lstar``: Lambda* of the starting opacities held fixed (else recomputed per iteration)."""
+    hist = np.zeros(max_iter, np.float32)
+    it = ctypes.c_int(0)
+    st = lib().rt_lambda_iterate_ali(grid.handle, ctypes.byref(atom.desc),
+                                     ctypes.byref(atm.desc), _dev(pops, (3, grid.npt), "pops"),
+                                     max_iter, float(tol), ctypes.byref(it),
+                                     hist.ctypes.data_as(L.PF), int(use_graph), int(newton),
+                                     int(bool(fixed_lstar)), _stream(stream))
+    if st not in (L.RT_OK, L.RT_ENOCONV):
+        check(st)
+    return it.value, hist[:it.value].copy(), st == L.RT_OK
+
+
 def emergent_intensity(grid, direction, alpha, S, bc=L.RT_BC_THERMAL, stream=None):
     nlam = alpha.shape[0]
     d = (ctypes.c_double * 3)(*[float(v) for v in direction])

@@ -299,70 +299,74 @@ __device__ inline void atomic_max_pos(float *addr, float v)
     atomicMax(reinterpret_cast<unsigned *>(addr), __float_as_uint(v));
 }
 
-// rates -> statistical equilibrium -> new populations and max |dn/n|
-__global__ void __launch_bounds__(256) se_kernel(int64_t npt, const float *T, const float *ne,
-                                                 const float *nH, const float *J, float *pops,
-                                                 float *dmax, unsigned *err)
+// Radiative rate coefficients of node j at one point: the node feeds transition lo -> hi with
+// R_lo,hi += fs J and R_hi,lo += fs g (2hc^2/lambda^5 + J).
+__device__ inline void node_rate(int j, float e, float kT, float tm32, const float *ph, float &fs,
+                                 float &g, int &lo, int &hi)
 {
-    __shared__ float tab[G_PIECES * G_DEG];
-    load_gtab(tab);
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const AtomDev &A = c_atom;
+    float sig;
+    if (A.kind[j] == 0) {
+        sig = A.c_line * ph[j];
+        g = A.g1_g2 * expf(A.dE_line[j] / kT);
+        lo = 0;
+        hi = 1;
+    } else {
+        const int i = A.kind[j] - 1;
+        sig = A.sig_bf[i][j];
+        g = e * A.saha_g[i] * A.saha_c * tm32 * expf(A.dchi[i][j] / kT);
+        lo = i;
+        hi = 2;
+    }
+    fs = A.rate_f[j] * sig;
+}
+
+__device__ inline void add_collisions(float (&P)[3][3], float t, float e, float kT, float tm32)
+{
+    const AtomDev &A = c_atom;
+    const float cb = A.q * e * rsqrtf(t);
+    P[1][0] += cb;
+    P[0][1] += cb * (1.f / A.g1_g2) * expf(-A.E21 / kT);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float cip = cb * expf(-A.chi[i] / kT);
+        P[i][2] += cip;
+        // C_pi = C_ip n_e Phi_i = cb n_e g_i/(2 g_p) saha_c T^-1.5 (exponentials cancel);
+        // n_e saha_c is formed first: cb n_e alone can exceed the FP32 range
+        P[2][i] += cb * ((e * A.saha_c) * tm32 * A.saha_g[i]);
+    }
+}
+
+// Steady state of the three-level rate matrix P (rates i -> j), scaled to n1 + n2 + np = nH.
+__device__ inline void mct_solve(float (&P)[3][3], float nH, float (&nn)[3])
+{
+    // scale to avoid FP32 range issues in the products
+    float m = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) m = fmaxf(m, P[a][b]);
+    const float s = 1.f / m;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) P[a][b] *= s;
+    // Markov-chain-tree steady state of three levels
+    const float t1 = P[1][0] * P[2][0] + P[1][2] * P[2][0] + P[2][1] * P[1][0];
+    const float t2 = P[0][1] * P[2][1] + P[0][2] * P[2][1] + P[2][0] * P[0][1];
+    const float t3 = P[0][2] * P[1][2] + P[0][1] * P[1][2] + P[1][0] * P[0][2];
+    const float f = nH / (t1 + t2 + t3);
+    nn[0] = t1 * f;
+    nn[1] = t2 * f;
+    nn[2] = t3 * f;
+}
+
+// new populations of one point: max |dn/n| into a block maximum, then one atomic per block
+__device__ inline void store_pops(int64_t npt, int64_t p, const float (&nn)[3], float *pops,
+                                  float *dmax, unsigned *err, bool active)
+{
     float change = 0.f;
-    if (p < npt) {
-        const AtomDev &A = c_atom;
-        const float t = T[p], e = ne[p], kT = t * 1.380649e-23f;
-        float ph[MAX_LAM];
-        line_profiles<float>(A.dld_coef * sqrtf(t), tab, ph);
-        const float tm32 = 1.f / (t * sqrtf(t));
-        float P[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-        for (int j = 0; j < A.nlam; ++j) {
-            const float Jj = J[(size_t)j * npt + p];
-            float sig, g;
-            int lo, hi;
-            if (A.kind[j] == 0) {
-                sig = A.c_line * ph[j];
-                g = A.g1_g2 * expf(A.dE_line[j] / kT);
-                lo = 0;
-                hi = 1;
-            } else {
-                const int i = A.kind[j] - 1;
-                sig = A.sig_bf[i][j];
-                g = e * A.saha_g[i] * A.saha_c * tm32 * expf(A.dchi[i][j] / kT);
-                lo = i;
-                hi = 2;
-            }
-            const float fs = A.rate_f[j] * sig;
-            P[lo][hi] += fs * Jj;
-            P[hi][lo] += fs * g * (A.b_l5[j] + Jj);
-        }
-        const float cb = A.q * e * rsqrtf(t);
-        P[1][0] += cb;
-        P[0][1] += cb * (1.f / A.g1_g2) * expf(-A.E21 / kT);
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            const float cip = cb * expf(-A.chi[i] / kT);
-            P[i][2] += cip;
-            // C_pi = C_ip n_e Phi_i = cb n_e g_i/(2 g_p) saha_c T^-1.5 (exponentials cancel);
-            // n_e saha_c is formed first: cb n_e alone can exceed the FP32 range
-            P[2][i] += cb * ((e * A.saha_c) * tm32 * A.saha_g[i]);
-        }
-        // scale to avoid FP32 range issues in the products
-        float m = 0.f;
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int b = 0; b < 3; ++b) m = fmaxf(m, P[a][b]);
-        const float s = 1.f / m;
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int b = 0; b < 3; ++b) P[a][b] *= s;
-        // Markov-chain-tree steady state of three levels
-        const float t1 = P[1][0] * P[2][0] + P[1][2] * P[2][0] + P[2][1] * P[1][0];
-        const float t2 = P[0][1] * P[2][1] + P[0][2] * P[2][1] + P[2][0] * P[0][1];
-        const float t3 = P[0][2] * P[1][2] + P[0][1] * P[1][2] + P[1][0] * P[0][2];
-        const float f = nH[p] / (t1 + t2 + t3);
-        const float nn[3] = {t1 * f, t2 * f, t3 * f};
+    if (active) {
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             const float old = pops[(size_t)i * npt + p];
@@ -374,7 +378,6 @@ __global__ void __launch_bounds__(256) se_kernel(int64_t npt, const float *T, co
             change = 0.f;
         }
     }
-    // block max, then one atomic per block
     __shared__ float red[8];
     float v = change;
     for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -386,6 +389,249 @@ __global__ void __launch_bounds__(256) se_kernel(int64_t npt, const float *T, co
         if (threadIdx.x == 0 && dmax) atomic_max_pos(dmax, v);
     }
 }
+
+// rates -> statistical equilibrium -> new populations and max |dn/n|
+__global__ void __launch_bounds__(256) se_kernel(int64_t npt, const float *T, const float *ne,
+                                                 const float *nH, const float *J, float *pops,
+                                                 float *dmax, unsigned *err)
+{
+    __shared__ float tab[G_PIECES * G_DEG];
+    load_gtab(tab);
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float nn[3] = {0.f, 0.f, 0.f};
+    if (p < npt) {
+        const AtomDev &A = c_atom;
+        const float t = T[p], e = ne[p], kT = t * 1.380649e-23f;
+        float ph[MAX_LAM];
+        line_profiles<float>(A.dld_coef * sqrtf(t), tab, ph);
+        const float tm32 = 1.f / (t * sqrtf(t));
+        float P[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+        for (int j = 0; j < A.nlam; ++j) {
+            const float Jj = J[(size_t)j * npt + p];
+            float fs, g;
+            int lo, hi;
+            node_rate(j, e, kT, tm32, ph, fs, g, lo, hi);
+            P[lo][hi] += fs * Jj;
+            P[hi][lo] += fs * g * (A.b_l5[j] + Jj);
+        }
+        add_collisions(P, t, e, kT, tm32);
+        mct_solve(P, nH[p], nn);
+    }
+    store_pops(npt, p, nn, pops, dmax, err, p < npt);
+}
+
+// Accelerated update (the point's own contribution to J treated implicitly): the populations n
+// with n = SE(J + Lambda* (S(n) - S_old)), by Newton's method on the logarithms of the two
+// smaller populations from the current ones (the largest follows from n1 + n2 + np = nH), with
+// a forward-difference Jacobian (step 1e-3 in log n).  A step that is not finite or leaves no
+// room for the largest population is replaced by the plain update; newton = 0 is the plain
+// update.  At a fixed point of the iteration the current populations solve the equation, so
+// the step is zero there.
+//
+// One warp per point: lane q holds wavelength nodes q and q + 32 (nlam <= 64), with the node's
+// opacity and emissivity as linear functions of (n1, n2, np) -- alpha = a0 + a1 n1 + a2 n2 +
+// ap np, eta = e0 + e2 n2 + ep np (the same terms as source_node) -- so one evaluation of the
+// rates costs a few multiply-adds per node and a warp reduction.  A block of 8 warps takes 32
+// consecutive points and stages their J, Lambda*, S_old rows through shared memory (coalesced).
+constexpr int ALI_PTS = 32, ALI_WARPS = 8;
+
+__global__ void __launch_bounds__(ALI_WARPS * 32) se_ali_kernel(
+    int64_t npt, const float *T, const float *rho, const float *ne, const float *nH,
+    const float *J, const float *L, const float *S_old, float *pops, float *dmax, unsigned *err,
+    int newton)
+{
+    __shared__ float tab[G_PIECES * G_DEG];
+    __shared__ float sJ[64][ALI_PTS], sL[64][ALI_PTS], sS[64][ALI_PTS];
+    __shared__ float red[ALI_WARPS];
+    // per-node atom constants: lanes read different nodes, which the constant cache serialises
+    enum { N_DLAM, N_WLINE, N_SB0, N_SB1, N_DEL, N_DCHI0, N_DCHI1, N_BL5, N_HCLK, N_RATEF, N_KIND,
+           N_COUNT };
+    __shared__ float snode[N_COUNT][64];
+    load_gtab(tab);
+    const AtomDev &A = c_atom;
+    const int nl = A.nlam;
+    for (int j = threadIdx.x; j < nl; j += blockDim.x) {
+        snode[N_DLAM][j] = A.dlam[j];
+        snode[N_WLINE][j] = A.wline[j];
+        snode[N_SB0][j] = A.sig_bf[0][j];
+        snode[N_SB1][j] = A.sig_bf[1][j];
+        snode[N_DEL][j] = A.dE_line[j];
+        snode[N_DCHI0][j] = A.dchi[0][j];
+        snode[N_DCHI1][j] = A.dchi[1][j];
+        snode[N_BL5][j] = A.b_l5[j];
+        snode[N_HCLK][j] = A.hc_lk[j];
+        snode[N_RATEF][j] = A.rate_f[j];
+        snode[N_KIND][j] = (float)A.kind[j];
+    }
+    const int64_t p0 = (int64_t)blockIdx.x * ALI_PTS;
+    for (int e = threadIdx.x; e < nl * ALI_PTS; e += blockDim.x) {
+        const int l = e / ALI_PTS, c = e % ALI_PTS;
+        const int64_t p = p0 + c;
+        const bool in = p < npt;
+        sJ[l][c] = in ? J[(size_t)l * npt + p] : 0.f;
+        sL[l][c] = in ? L[(size_t)l * npt + p] : 0.f;
+        sS[l][c] = in ? S_old[(size_t)l * npt + p] : 0.f;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float wmax = 0.f;
+    for (int c = warp; c < ALI_PTS; c += ALI_WARPS) {
+        const int64_t p = p0 + c;
+        if (p >= npt) break;
+        const float t = T[p], r = rho[p], e = ne[p], nh = nH[p], kT = t * 1.380649e-23f;
+        const float tm32 = 1.f / (t * sqrtf(t));
+        const float t5 = t * (1.f / 5000.f);
+        float t9 = t5 * t5;
+        t9 = t9 * t9;
+        t9 = t9 * t9 * t5;
+        const float abg = A.kappa0 * r * t9;
+        // line profile of this point, normalised over the line nodes
+        const float dld = A.dld_coef * sqrtf(t), inv = 1.f / dld;
+        float phr[2] = {0.f, 0.f}, psum = 0.f;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int j = lane + 32 * q;
+            if (j < nl && snode[N_KIND][j] == 0.f) {
+                phr[q] = voigt_H<float>(A.a, snode[N_DLAM][j] * inv, tab) * 0.56418958354775628f * inv;
+                psum += snode[N_WLINE][j] * phr[q];
+            }
+        }
+        for (int o = 16; o; o >>= 1) psum += __shfl_xor_sync(0xffffffffu, psum, o);
+        const float ninv = 1.f / psum;
+        // per node: linear opacity and emissivity, rate coefficients, J_eff and Lambda*
+        float ca0[2], ca1[2], ca2[2], cap[2], ce0[2], ce2[2], cep[2], jef[2], lst[2], fs[2],
+            fsg[2], fsgb[2];
+        int tr[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int j = lane + 32 * q;
+            tr[q] = -1;
+            if (j >= nl) continue;
+            const int kd = (int)snode[N_KIND][j];
+            const float bl5 = snode[N_BL5][j];
+            const float B = bl5 / expm1f(snode[N_HCLK][j] / t);   // as planck_dev
+            const float sigl = kd == 0 ? A.c_line * phr[q] * ninv : 0.f;
+            const float gl = kd == 0 ? A.g1_g2 * expf(snode[N_DEL][j] / kT) : 0.f;
+            float sb[2], gb[2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                sb[i] = snode[N_SB0 + i][j];
+                gb[i] = sb[i] == 0.f ? 0.f
+                                     : (e * A.saha_g[i] * A.saha_c) * tm32 *
+                                           expf(snode[N_DCHI0 + i][j] / kT);
+            }
+            ca0[q] = abg;
+            ca1[q] = sigl + sb[0];
+            ca2[q] = sb[1] - sigl * gl;
+            cap[q] = -(sb[0] * gb[0] + sb[1] * gb[1]);
+            ce0[q] = abg * B;
+            ce2[q] = bl5 * sigl * gl;
+            cep[q] = bl5 * (sb[0] * gb[0] + sb[1] * gb[1]);
+            lst[q] = sL[j][c];
+            jef[q] = sJ[j][c] - lst[q] * sS[j][c];
+            const float sig = kd == 0 ? sigl : (kd == 1 ? sb[0] : sb[1]);
+            const float gg = kd == 0 ? gl : (kd == 1 ? gb[0] : gb[1]);
+            fs[q] = snode[N_RATEF][j] * sig;
+            fsg[q] = fs[q] * gg;
+            fsgb[q] = fsg[q] * bl5;
+            tr[q] = kd;
+        }
+        // collisional rates: independent of the populations
+        float Pc[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+        add_collisions(Pc, t, e, kT, tm32);
+        // the plain update with the radiation of the populations n (identical in every lane)
+        auto G = [&](const float (&n)[3], float (&out)[3]) {
+            float up[3] = {0.f, 0.f, 0.f}, dn[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                if (tr[q] < 0) continue;
+                const float al = ca0[q] + ca1[q] * n[0] + ca2[q] * n[1] + cap[q] * n[2];
+                const float et = ce0[q] + ce2[q] * n[1] + cep[q] * n[2];
+                const float Jj = jef[q] + lst[q] * (et / al);
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+                    if (tr[q] == k) {
+                        up[k] += fs[q] * Jj;
+                        dn[k] += fsg[q] * Jj + fsgb[q];
+                    }
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                for (int o = 16; o; o >>= 1) {
+                    up[k] += __shfl_xor_sync(0xffffffffu, up[k], o);
+                    dn[k] += __shfl_xor_sync(0xffffffffu, dn[k], o);
+                }
+            float P[3][3] = {{0.f, up[0] + Pc[0][1], up[1] + Pc[0][2]},
+                             {dn[0] + Pc[1][0], 0.f, up[2] + Pc[1][2]},
+                             {dn[1] + Pc[2][0], dn[2] + Pc[2][1], 0.f}};
+            mct_solve(P, nh, out);
+        };
+        const float cur[3] = {pops[p], pops[npt + p], pops[2 * npt + p]};
+        float nn[3];
+        if (newton == 0) {
+            G(cur, nn);
+        } else {
+            const int big = (cur[0] >= cur[1] && cur[0] >= cur[2]) ? 0 : (cur[1] >= cur[2] ? 1 : 2);
+            const int s0 = big == 0 ? 1 : 0, s1 = big == 2 ? 1 : 2;
+            // runtime level indices through selects (an indexed array would live in local memory)
+            auto pick = [](const float (&v)[3], int i) { return i == 0 ? v[0] : (i == 1 ? v[1] : v[2]); };
+            float x[2] = {pick(cur, s0), pick(cur, s1)};
+            auto full = [&](const float (&xx)[2], float (&n)[3]) {
+                const float rest = nh - xx[0] - xx[1];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) n[k] = k == big ? rest : (k == s0 ? xx[0] : xx[1]);
+            };
+            const float h = 1e-3f, eh = expf(h);
+            for (int it = 0; it < newton; ++it) {
+                float n[3], g0[3];
+                full(x, n);
+                G(n, g0);
+                const float H0[2] = {logf(pick(g0, s0)) - logf(x[0]), logf(pick(g0, s1)) - logf(x[1])};
+                float Jm[2][2];
+#pragma unroll
+                for (int cc = 0; cc < 2; ++cc) {
+                    float xp[2] = {x[0], x[1]};
+                    xp[cc] *= eh;
+                    float np_[3], gp[3];
+                    full(xp, np_);
+                    G(np_, gp);
+                    Jm[0][cc] = (logf(pick(gp, s0)) - logf(xp[0]) - H0[0]) / h;
+                    Jm[1][cc] = (logf(pick(gp, s1)) - logf(xp[1]) - H0[1]) / h;
+                }
+                const float det = Jm[0][0] * Jm[1][1] - Jm[0][1] * Jm[1][0];
+                const float st0 = (Jm[1][1] * H0[0] - Jm[0][1] * H0[1]) / det;
+                const float st1 = (-Jm[1][0] * H0[0] + Jm[0][0] * H0[1]) / det;
+                const float xn0 = x[0] * expf(-st0), xn1 = x[1] * expf(-st1);
+                const bool bad = !isfinite(xn0) || !isfinite(xn1) || !(xn0 + xn1 < nh);
+                x[0] = bad ? pick(g0, s0) : xn0;
+                x[1] = bad ? pick(g0, s1) : xn1;
+            }
+            full(x, nn);
+        }
+        if (lane == 0) {
+            float change = 0.f;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                change = fmaxf(change, fabsf(nn[i] - cur[i]) / nn[i]);
+                pops[(size_t)i * npt + p] = nn[i];
+            }
+            if (!isfinite(change)) {
+                flag_error(err, ERR_NAN);
+                change = 0.f;
+            }
+            wmax = fmaxf(wmax, change);
+        }
+    }
+    if (lane == 0) red[warp] = wmax;
+    __syncthreads();
+    if (threadIdx.x == 0 && dmax) {
+        float v = 0.f;
+        for (int w = 0; w < ALI_WARPS; ++w) v = fmaxf(v, red[w]);
+        atomic_max_pos(dmax, v);
+    }
+}
+
+static inline unsigned ali_blocks(int64_t n) { return (unsigned)((n + ALI_PTS - 1) / ALI_PTS); }
 
 __global__ void lte_source_kernel(int64_t npt, const float *T, const float *rho, float kappa0,
                                   float b_l5, float hc_lk, float *alpha, float *S)
@@ -584,9 +830,31 @@ rt_status rt_statistical_equilibrium(rt_grid_t g, const rt_atom *atom, const rt_
     return RT_OK;
 }
 
-rt_status rt_lambda_iterate(rt_grid_t g, const rt_atom *atom, const rt_atmos *atm, float *pops,
-                            int max_iter, double tol, int *iters_out, float *history,
-                            int use_graph, void *stream)
+rt_status rt_statistical_equilibrium_ali(rt_grid_t g, const rt_atom *atom, const rt_atmos *atm,
+                                         const float *J, const float *Lstar, const float *S_old,
+                                         float *pops, float *dmax_dev, int newton, void *stream)
+{
+    RT_TRY(check_atmos(g, atm, pops));
+    if (!J || !Lstar || !S_old) return fail(RT_EINVAL, "null J, Lstar or S_old");
+    if (newton < 0 || newton > 16) return fail(RT_EINVAL, "newton must be in 0..16");
+    if (atom->nlam > 64) return fail(RT_EINVAL, "the accelerated update takes at most 64 wavelengths");
+    RT_TRY(load_atom(atom));
+    const int64_t n = g->npt;
+    note_launch();
+    se_ali_kernel<<<ali_blocks(n), ALI_WARPS * 32, 0, (cudaStream_t)stream>>>(
+        n, atm->T, atm->rho, atm->ne, atm->nH, J, Lstar, S_old, pops, dmax_dev, g->d_err, newton);
+    RT_CUDA(cudaGetLastError());
+    return RT_OK;
+}
+
+}  // extern "C"
+
+// The Lambda iteration loop; newton < 0: plain, else accelerated with that many Newton steps
+// and Lambda* either from the starting opacities, held fixed (fixed_lstar), or recomputed from
+// every iteration's opacities.
+static rt_status iterate(rt_grid_t g, const rt_atom *atom, const rt_atmos *atm, float *pops,
+                         int max_iter, double tol, int *iters_out, float *history, int use_graph,
+                         int newton, int fixed_lstar, void *stream)
 {
     RT_TRY(check_atmos(g, atm, pops));
     if (max_iter < 1) return fail(RT_EINVAL, "max_iter must be >= 1");
@@ -594,11 +862,15 @@ rt_status rt_lambda_iterate(rt_grid_t g, const rt_atom *atom, const rt_atmos *at
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t n = g->npt;
     const int nlam = atom->nlam;
-    // scratch 2: alpha, S, J [nlam][n] + dmax
+    // scratch 2: alpha, S, J [nlam][n] (+ Lambda* when accelerated) + dmax
+    const bool ali = newton >= 0;
+    const size_t nf = (ali ? 4 : 3) * (size_t)nlam * n;
     void *p;
-    RT_TRY(scratch_get(g, 2, 3 * (size_t)nlam * n * sizeof(float) + 256, &p));
+    RT_TRY(scratch_get(g, 2, nf * sizeof(float) + 256, &p));
     float *alpha = (float *)p, *S = alpha + (size_t)nlam * n, *J = S + (size_t)nlam * n;
-    float *dmax = J + (size_t)nlam * n;
+    float *L = ali ? J + (size_t)nlam * n : nullptr;
+    float *dmax = (float *)p + nf;
+    if (ali) RT_TRY(lambda_star_prepare(g));
     dmax = (float *)(((uintptr_t)dmax + 15) & ~(uintptr_t)15);
     float *h_dmax = nullptr;
     RT_CUDA(cudaMallocHost(&h_dmax, sizeof(float)));
@@ -620,11 +892,25 @@ rt_status rt_lambda_iterate(rt_grid_t g, const rt_atom *atom, const rt_atmos *at
             n, atm->T, atm->rho, atm->ne, pops, alpha, S, g->d_err);
         RT_TRY(rt_formal_solution(g, nlam, alpha, S, RT_BC_THERMAL, nullptr, J, nullptr, st));
         note_launch();
-        se_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, atm->T, atm->ne, atm->nH, J,
-                                                                pops, dmax, g->d_err);
+        if (ali) {
+            if (!fixed_lstar) RT_TRY(lambda_star(g, nlam, alpha, RT_BC_THERMAL, L, st));
+            se_ali_kernel<<<ali_blocks(n), ALI_WARPS * 32, 0, st>>>(
+                n, atm->T, atm->rho, atm->ne, atm->nH, J, L, S, pops, dmax, g->d_err, newton);
+        } else {
+            se_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, atm->T, atm->ne, atm->nH,
+                                                                    J, pops, dmax, g->d_err);
+        }
         RT_CUDA(cudaMemcpyAsync(h_dmax, dmax, sizeof(float), cudaMemcpyDeviceToHost, st));
         return RT_OK;
     };
+    if (ali && fixed_lstar) {
+        // Lambda* of the starting populations' opacities, held fixed: the fixed point of the
+        // iteration does not depend on Lambda*, only its rate of convergence does
+        note_launch();
+        source_terms_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(
+            n, atm->T, atm->rho, atm->ne, pops, alpha, S, g->d_err);
+        RT_TRY(lambda_star(g, nlam, alpha, RT_BC_THERMAL, L, st));
+    }
     cudaStream_t cs = nullptr;       // capture stream (the legacy default stream cannot be captured)
     cudaEvent_t ev = nullptr;
     struct StreamGuard {
@@ -680,6 +966,28 @@ rt_status rt_lambda_iterate(rt_grid_t g, const rt_atom *atom, const rt_atmos *at
     if (iters_out) *iters_out = std::min(it, max_iter);
     if (result == RT_ENOCONV) fail(RT_ENOCONV, "max_iter reached before the tolerance");
     return result;
+}
+
+extern "C" {
+
+rt_status rt_lambda_iterate(rt_grid_t g, const rt_atom *atom, const rt_atmos *atm, float *pops,
+                            int max_iter, double tol, int *iters_out, float *history,
+                            int use_graph, void *stream)
+{
+    return iterate(g, atom, atm, pops, max_iter, tol, iters_out, history, use_graph, -1, 0,
+                   stream);
+}
+
+rt_status rt_lambda_iterate_ali(rt_grid_t g, const rt_atom *atom, const rt_atmos *atm,
+                                float *pops, int max_iter, double tol, int *iters_out,
+                                float *history, int use_graph, int newton, int fixed_lstar,
+                                void *stream)
+{
+    if (newton < 0 || newton > 16) return fail(RT_EINVAL, "newton must be in 0..16");
+    if (atom && atom->nlam > 64)
+        return fail(RT_EINVAL, "the accelerated update takes at most 64 wavelengths");
+    return iterate(g, atom, atm, pops, max_iter, tol, iters_out, history, use_graph, newton,
+                   fixed_lstar, stream);
 }
 
 // Host evaluation of the device Voigt function for testing: H(a, v) in FP32 arithmetic is not

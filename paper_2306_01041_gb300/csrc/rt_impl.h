@@ -121,6 +121,7 @@ struct rt_grid {
     std::vector<int8_t> nbr_shift;
     rt::VorTables vt;                          // the quadrature directions
     rt::VorTables vt_one;                      // cache: one extra direction (emergent/adjoint)
+    rt::Upwind *d_up_site = nullptr;           // [ndir][nsites] records in site order (Lambda*)
     rt_batch *self_batch = nullptr;            // persistent all-direction sweep of this grid alone
     int self_batch_nlam = 0;
     int64_t n_fallback = 0;
@@ -150,6 +151,10 @@ size_t regular_wave_scratch(const rt_grid *g, int nlam);
 // Voronoi: builds what the formal solution of nlam wavelengths allocates on first use (call
 // outside stream capture)
 rt_status voronoi_prepare(rt_grid *g, int nlam);
+// Lambda* [nlam][npt] (diagonal of the Lambda operator) of the opacities alpha
+rt_status lambda_star(rt_grid *g, int nlam, const float *alpha, int bc, float *L, cudaStream_t st);
+// allocates what lambda_star needs on first use (call outside stream capture)
+rt_status lambda_star_prepare(rt_grid *g);
 // builds and uploads the wavefront sweep's per-plane stencil table (no-op where it cannot apply)
 rt_status regular_wave_prepare(rt_grid *g, cudaStream_t st);
 rt_status regular_emergent(rt_grid *g, const double *dir, int nlam, const float *alpha,

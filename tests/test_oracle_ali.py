@@ -89,3 +89,7 @@ def test_ali_reaches_the_lambda_fixed_point_in_fewer_iterations():
     assert it_a < it_l / 2, (it_a, it_l)
     np.testing.assert_allclose(ali, ref, rtol=2e-5)
     assert hist[-1] < 1e-7
+    # Lambda* of the starting opacities held fixed, one Newton step: the same fixed point
+    fx, it_f, _ = ali_iterate(*args, max_iter=300, tol=1e-7, newton=1, fixed_lstar=True)
+    assert it_f < it_l / 2, (it_f, it_l)
+    np.testing.assert_allclose(fx, ref, rtol=2e-5)
