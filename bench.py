@@ -494,6 +494,32 @@ def run_extras(torch, rt, dev):
     return out
 
 
+def run_iterate(args):
+    """Time to convergence of the Lambda iteration or the accelerated one on the NX^3 regular
+    grid (from LTE, max |dn/n| < --tol or --max-iter iterations).  Prints one JSON line."""
+    import torch
+    import paper_2306_01041_gb300 as rt
+    dev = torch.device("cuda", 0)
+    atm, f, (x, y, z, dx, dy), data, dirs, w = setup_problem(torch, dev)
+    g = rt.RegularGrid(NX, NY, NZ, dx, dy, z, dirs, w)
+    A = rt.Atom(data, atm.kappa0)
+    M = rt.Atmos(*[torch.tensor(f[k], dtype=torch.float32, device=dev)
+                   for k in ("T", "rho", "ne", "nH")])
+    fn = rt.lambda_iterate_ali if args.iterate == "ali" else rt.lambda_iterate
+    pops = rt.lte_populations(g, A, M)
+    fn(g, A, M, pops, max_iter=1, tol=args.tol)              # first-call set-up, untimed
+    pops = rt.lte_populations(g, A, M)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    it, hist, conv = fn(g, A, M, pops, max_iter=args.max_iter, tol=args.tol)
+    dt = time.perf_counter() - t
+    print(json.dumps({"workload": f"{args.iterate} iteration, regular grid {NX}x{NY}x{NZ}, "
+                                  f"{len(data['lam'])} wavelengths", "iterations": it,
+                      "converged": bool(conv), "seconds": round(dt, 4),
+                      "ms_per_iteration": round(dt / it * 1e3, 3),
+                      "final_change": float(hist[-1])}))
+
+
 def run_voronoi_batch(args):
     """The batched Voronoi formal solution alone on the first N atmospheres of the 8-atmosphere
     workload (52 wavelengths, 24 directions, populations at LTE): a smaller case of the batched
@@ -660,6 +686,10 @@ def main():
     ap.add_argument("--voronoi-batch", type=int, default=0,
                     help="time only the batched Voronoi formal solution on the first N of the 8 "
                          "atmospheres (a smaller case for profiling)")
+    ap.add_argument("--iterate", choices=["lambda", "ali"], default=None,
+                    help="time the Lambda iteration or the accelerated one to convergence")
+    ap.add_argument("--max-iter", type=int, default=300)
+    ap.add_argument("--tol", type=float, default=1e-3)
     ap.add_argument("--z-stretch", type=float, default=0.0,
                     help="non-uniform z spacing amplitude a in [0, 1) (cell heights (1 -+ a) dz)")
     args = ap.parse_args()
@@ -673,6 +703,9 @@ def main():
         args.warmup = 3
     if args.voronoi_batch:
         run_voronoi_batch(args)
+        return
+    if args.iterate:
+        run_iterate(args)
         return
     if args.impl == "reference":
         run_reference(args)

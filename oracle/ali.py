@@ -3,8 +3,7 @@
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
 The paper iterates plain Lambda (Sect. 2.1: populations -> source functions -> formal solution ->
-J -> statistical equilibrium) and notes in its introduction that accelerated schemes converge in
-far fewer iterations.  This module states the accelerated scheme used here, in FP64:
+J -> statistical equilibrium) and notes there that accelerated schemes converge much faster.  This module states the accelerated scheme used here, in FP64:
 
 Lambda* [nlam][npt]
     dJ_p / dS_p with the opacities fixed: the diagonal of the linear map S -> J of the formal
