@@ -435,7 +435,7 @@ __global__ void __launch_bounds__(256) se_kernel(int64_t npt, const float *T, co
 // consecutive points and stages their J, Lambda*, S_old rows through shared memory (coalesced).
 constexpr int ALI_PTS = 32, ALI_WARPS = 8;
 
-__global__ void __launch_bounds__(ALI_WARPS * 32) se_ali_kernel(
+__global__ void __launch_bounds__(ALI_WARPS * 32, 3) se_ali_kernel(
     int64_t npt, const float *T, const float *rho, const float *ne, const float *nH,
     const float *J, const float *L, const float *S_old, float *pops, float *dmax, unsigned *err,
     int newton)
