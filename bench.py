@@ -491,7 +491,34 @@ def run_extras(torch, rt, dev):
     out["adjoint"] = adjoint_timing(torch, rt, dev)
     out["adjoint_voronoi_200k"] = voronoi_adjoint_timing(torch, rt, dev, *extra[9], dirs, w)
     out["lte_continuum"] = lte_continuum_timing(torch, rt, dev, *extra[10], dirs, w)
+    out["final_synthesis"] = synthesis_timing(torch, rt, dev, *extra[9], dirs, w)
     return out
+
+
+def synthesis_timing(torch, rt, dev, g, f, kappa0, dirs, w):
+    """The paper's final synthesis from the 200k-site grid (populations at LTE) to the 128^3
+    mesh: two-nearest table (host, once), interpolation of the populations, source terms and the
+    vertical long-characteristics formal solution on the mesh (52 wavelengths)."""
+    from synth import make_atmosphere, model_atom
+    from synth.atmosphere import regular_fields
+    atm = make_atmosphere(0)
+    mf, (x, y, z, dx, dy) = regular_fields(NX, NY, NZ, atm)
+    G = rt.VoronoiGrid(g["xyz"], g["nbr_off"], g["nbr_idx"], g["nbr_shift"], g["box"], dirs, w)
+    mesh = rt.RegularGrid(NX, NY, NZ, dx, dy, z, dirs, w)
+    A = rt.Atom(model_atom(np.min(mf["ne"] / np.sqrt(mf["T"]))), atm.kappa0)
+    sv = rt.Atmos(*[torch.tensor(f[k], dtype=torch.float32, device=dev)
+                    for k in ("T", "rho", "ne", "nH")])
+    mv = rt.Atmos(*[torch.tensor(mf[k], dtype=torch.float32, device=dev)
+                    for k in ("T", "rho", "ne", "nH")])
+    site_pops = rt.lte_populations(G, A, sv)
+    t = time.perf_counter()
+    idw = rt.IDW(G, mesh)
+    build_s = time.perf_counter() - t
+    res = {"sites": G.npt, "mesh": [NX, NY, NZ], "table_build_s": round(build_s, 3),
+           "interpolate_ms": round(_events(torch, lambda: idw.interpolate(site_pops)), 3),
+           "final_synthesis_ms": round(_events(torch, lambda: rt.final_synthesis(
+               idw, mesh, A, mv, site_pops)), 3)}
+    return res
 
 
 def run_iterate(args):

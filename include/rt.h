@@ -208,6 +208,27 @@ rt_status rt_lambda_iterate_ali(rt_grid_t grid, const rt_atom *atom, const rt_at
                                 float *history, int use_graph, int newton, int fixed_lstar,
                                 void *stream);
 
+/* ---- final synthesis on a Voronoi grid (Sect. 2.5, last paragraphs) ---------------------------
+ * The paper takes the emergent intensity not from the irregular grid, whose upper layers hold few
+ * sites, but from the original mesh: the converged populations are interpolated to the mesh by
+ * inverse-distance weighting over the two nearest sites (weights 1/d normalised; (1, 0) on a
+ * site), and a formal solution along vertical long characteristics follows (rt_emergent_intensity
+ * with dir = (0, 0, 1) on the regular grid, whose rays then run along the mesh columns). */
+typedef struct rt_idw *rt_idw_t;
+
+/* Two-nearest table of every point of `mesh` (a regular grid; point (i, j, k) at (i dx, j dy,
+ * z_k) in the sites' frame) among the sites of `voronoi`: exact, minimum-image distances in the
+ * periodic x and y, ties to the smaller site index.  Built on the host (OpenMP) and uploaded;
+ * synchronous.  *out is owned by the caller (rt_idw_destroy). */
+rt_status rt_idw_create(rt_grid_t voronoi, rt_grid_t mesh, rt_idw_t *out);
+void rt_idw_destroy(rt_idw_t table);
+
+/* The table on the host: k [npt][2] site indices, w [npt][2] weights (caller-owned arrays). */
+rt_status rt_idw_table(rt_idw_t table, int32_t *k, float *w);
+
+/* dst [nf][npt_mesh] = w1 src[nf][k1] + w2 src[nf][k2] (device arrays; src [nf][nsites]). */
+rt_status rt_idw_interpolate(rt_idw_t table, int nf, const float *src, float *dst, void *stream);
+
 /* ---- emergent intensity and its adjoint (Sect. 2.5-2.6; Eq. 2 differentiated) -------------- */
 /* Intensity along one direction dir[3] (mu_z > 0) at the emergent layer:
  * I_top [nlam][ntop] (device).  Regular grid: the top plane.  Voronoi grid: the sites listed by

@@ -5,8 +5,9 @@ Build the library first (``python -c "import __graft_entry__ as g; g.build()"`` 
 ``python paper_2306_01041_gb300/build.py``); importing the API raises if it is missing.
 """
 from ._lib import (RT_BC_ARRAY, RT_BC_THERMAL, RT_BC_ZERO, RTError, lib)  # noqa: F401
-from .api import (Atmos, Atom, Batch, EmergentIntensity, Grid, RegularGrid,  # noqa: F401
-                  VoronoiGrid, emergent_intensity, formal_solution, formal_solution_adjoint,
+from .api import (IDW, Atmos, Atom, Batch, EmergentIntensity, Grid, RegularGrid,  # noqa: F401
+                  VoronoiGrid, emergent_intensity, final_synthesis, formal_solution,
+                  formal_solution_adjoint,
                   kernel_launches, lambda_iterate, lambda_iterate_ali, lambda_star,
                   lte_populations, source_terms, source_terms_adjoint, source_terms_lte,
                   source_terms_lte_adjoint, statistical_equilibrium, statistical_equilibrium_ali)

@@ -80,6 +80,10 @@ SIGNATURES = {
     "rt_lambda_iterate_ali": (c_int, [P, ctypes.POINTER(AtomDesc), ctypes.POINTER(AtmosDesc), P,
                                       c_int, c_double, ctypes.POINTER(c_int), PF, c_int, c_int,
                                       c_int, P]),
+    "rt_idw_create": (c_int, [P, P, ctypes.POINTER(P)]),
+    "rt_idw_destroy": (None, [P]),
+    "rt_idw_table": (c_int, [P, PI32, PF]),
+    "rt_idw_interpolate": (c_int, [P, c_int, P, P, P]),
     "rt_emergent_intensity": (c_int, [P, PD, c_int, P, P, c_int, P, P]),
     "rt_adjoint_workspace_size": (c_size_t, [P, c_int, c_int]),
     "rt_formal_solution_adjoint": (c_int, [P, PD, c_int, P, P, c_int, P, P, P, c_int, P, c_size_t,

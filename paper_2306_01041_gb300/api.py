@@ -292,6 +292,47 @@ def lambda_iterate_ali(grid, atom: Atom, atm: Atmos, pops, max_iter=300, tol=1e-
     return it.value, hist[:it.value].copy(), st == L.RT_OK
 
 
+class IDW:
+    """Two-nearest inverse-distance interpolation from a Voronoi grid's sites to a regular mesh
+    (the final synthesis of Sect. 2.5)."""
+
+    def __init__(self, voronoi, mesh):
+        h = ctypes.c_void_p()
+        check(lib().rt_idw_create(voronoi.handle, mesh.handle, ctypes.byref(h)))
+        self._h = h
+        self.nsites, self.npt = voronoi.npt, mesh.npt
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and L._lib is not None:
+            L._lib.rt_idw_destroy(h)
+            self._h = None
+
+    def table(self):
+        """(k [npt][2] int32, w [npt][2] float32) on the host."""
+        k = np.empty((self.npt, 2), np.int32)
+        w = np.empty((self.npt, 2), np.float32)
+        check(lib().rt_idw_table(self._h, k.ctypes.data_as(L.PI32), w.ctypes.data_as(L.PF)))
+        return k, w
+
+    def interpolate(self, src, out=None, stream=None):
+        nf = src.shape[0]
+        dst = torch.empty((nf, self.npt), device=src.device, dtype=torch.float32) \
+            if out is None else out
+        check(lib().rt_idw_interpolate(self._h, nf, _dev(src, (nf, self.nsites), "src"),
+                                       _dev(dst, (nf, self.npt), "dst"), _stream(stream)))
+        return dst
+
+
+def final_synthesis(idw: IDW, mesh, atom: Atom, mesh_atm: Atmos, site_pops, stream=None):
+    """Emergent vertical intensity [nlam][nx ny] of the mesh from converged site populations:
+    interpolation to the mesh, opacities and source functions there, long characteristics
+    along mu = 1."""
+    pops = idw.interpolate(site_pops, stream=stream)
+    alpha, S = source_terms(mesh, atom, mesh_atm, pops, stream=stream)
+    return emergent_intensity(mesh, (0.0, 0.0, 1.0), alpha, S, stream=stream)
+
+
 def emergent_intensity(grid, direction, alpha, S, bc=L.RT_BC_THERMAL, stream=None):
     nlam = alpha.shape[0]
     d = (ctypes.c_double * 3)(*[float(v) for v in direction])
