@@ -146,15 +146,49 @@ __device__ __forceinline__ void tile_updates(const TileArgs &a, const WaveSt *st
     }
 }
 
+// S and alpha of an item's upwind plane into the shared (S, alpha) pairs (slot x holds x and
+// x + 1), with halo; returns the smallest alpha this thread staged.  No dependency on other
+// items: the persistent kernel issues these loads while it waits for the upwind intensities.
+template <int HY>
+__device__ __forceinline__ float tile_stage_sa(const TileArgs &a, const PlaneCtx &c, int l, int x0,
+                                               int y0, float *smt, int ndh)
+{
+    const int hy = HY > 0 ? HY : a.hy;
+    const int ph = TL_H + 2 * hy, tsz = TL_PW * ph, q4 = TL_PW / 4;
+    float4 *SA = reinterpret_cast<float4 *>(smt + (size_t)ndh * tsz);
+    const size_t npt = (size_t)a.np * a.nz;
+    const float *Su = a.S + (size_t)l * npt + (size_t)c.ku * a.np;
+    const float *Au = a.alpha + (size_t)l * npt + (size_t)c.ku * a.np;
+    float amin = __int_as_float(0x7f800000);
+    for (int e = threadIdx.x; e < ph * q4; e += TL_THREADS) {
+        const int r = e / q4, c4 = e % q4;
+        const int gy = wrapi(y0 - hy + r, a.ny, a.wrap1);
+        const int gx = wrapi(x0 - TL_HXP + 4 * c4, a.nx, a.wrap1);
+        const int gx4 = wrapi(gx + 4, a.nx, true);
+        const size_t g = (size_t)gy * a.nx + gx, g4 = (size_t)gy * a.nx + gx4;
+        const float4 sv = __ldg(reinterpret_cast<const float4 *>(Su + g));
+        const float4 av = __ldg(reinterpret_cast<const float4 *>(Au + g));
+        const float s4 = __ldg(Su + g4), a4 = __ldg(Au + g4);
+        float4 *sa = SA + r * TL_PW + 4 * c4;
+        sa[0] = make_float4(sv.x, av.x, sv.y, av.y);
+        sa[1] = make_float4(sv.y, av.y, sv.z, av.z);
+        sa[2] = make_float4(sv.z, av.z, sv.w, av.w);
+        sa[3] = make_float4(sv.w, av.w, s4, a4);
+        amin = fminf(amin, fminf(fminf(av.x, av.y), fminf(av.z, av.w)));
+    }
+    return amin;
+}
+
 // One (tile, wavelength) item of one plane step.  WAVE selects the persistent kernel's variant:
 // L2-coherent loads of the upwind intensities (planes written by other blocks of the same launch,
 // which the non-coherent read-only path could serve stale) and its tile-major intensity ring
 // [nlam][ntiles][ndh][TL_H][TL_W]; otherwise the ring is [nlam][ndh][nx * ny].  PP: the plane's
 // stencils come from the table gst (copied to the shared sts), else from the arguments.
-template <int NDH, bool WAVE, bool PP, int HY = 0>
+// SA_DONE: the (S, alpha) pairs were staged before (tile_stage_sa), amin_in their minimum alpha.
+template <int NDH, bool WAVE, bool PP, int HY = 0, bool SA_DONE = false>
 __device__ __forceinline__ void tile_item(const TileArgs &a, const PlaneCtx &c, int l, int tile,
                                           int x0, int y0, float *smt, const WaveSt *gst,
-                                          WaveSt *sts)
+                                          WaveSt *sts, float amin_in = 0.f)
 {
     const int ndh = NDH > 0 ? NDH : a.ndh;
     const int hy = HY > 0 ? HY : a.hy;                       // compile-time where HY > 0
@@ -174,23 +208,25 @@ __device__ __forceinline__ void tile_item(const TileArgs &a, const PlaneCtx &c, 
     if (PP && tid < NDH * 8)
         reinterpret_cast<int *>(sts)[tid] = __ldg(reinterpret_cast<const int *>(gst) + tid);
     const float hds_min = PP ? __ldg(&gst->hds_min) : a.hds_min;
-    float amin = __int_as_float(0x7f800000);
+    float amin = SA_DONE ? amin_in : __int_as_float(0x7f800000);
     for (int e = tid; e < ph * q4; e += TL_THREADS) {
         const int r = e / q4, c4 = e % q4;
         const int gy = wrapi(y0 - hy + r, a.ny, a.wrap1);
         const int gx = wrapi(x0 - TL_HXP + 4 * c4, a.nx, a.wrap1);
-        const int gx4 = wrapi(gx + 4, a.nx, true);
         const size_t g = (size_t)gy * a.nx + gx;
-        const size_t g4 = (size_t)gy * a.nx + gx4;
-        const float4 sv = __ldg(reinterpret_cast<const float4 *>(Su + g));
-        const float4 av = __ldg(reinterpret_cast<const float4 *>(Au + g));
-        const float s4 = __ldg(Su + g4), a4 = __ldg(Au + g4);
-        float4 *sa = SA + r * TL_PW + 4 * c4;
-        sa[0] = make_float4(sv.x, av.x, sv.y, av.y);
-        sa[1] = make_float4(sv.y, av.y, sv.z, av.z);
-        sa[2] = make_float4(sv.z, av.z, sv.w, av.w);
-        sa[3] = make_float4(sv.w, av.w, s4, a4);
-        amin = fminf(amin, fminf(fminf(av.x, av.y), fminf(av.z, av.w)));
+        if (!SA_DONE) {
+            const int gx4 = wrapi(gx + 4, a.nx, true);
+            const size_t g4 = (size_t)gy * a.nx + gx4;
+            const float4 sv = __ldg(reinterpret_cast<const float4 *>(Su + g));
+            const float4 av = __ldg(reinterpret_cast<const float4 *>(Au + g));
+            const float s4 = __ldg(Su + g4), a4 = __ldg(Au + g4);
+            float4 *sa = SA + r * TL_PW + 4 * c4;
+            sa[0] = make_float4(sv.x, av.x, sv.y, av.y);
+            sa[1] = make_float4(sv.y, av.y, sv.z, av.z);
+            sa[2] = make_float4(sv.z, av.z, sv.w, av.w);
+            sa[3] = make_float4(sv.w, av.w, s4, a4);
+            amin = fminf(amin, fminf(fminf(av.x, av.y), fminf(av.z, av.w)));
+        }
         const float *src0;
         size_t dstep;
         if (WAVE) {
@@ -406,21 +442,23 @@ __global__ void __launch_bounds__(TL_THREADS, 2) sc_wave_kernel(WaveArgs w)
             const bool ok = __all_sync(0xffffffffu, f ? wait_flag(f, a.err) : true);
             if (lane == 0 && !ok) flag_error(a.err, ERR_TIMEOUT);
         }
+        // S and alpha of the upwind plane depend on no other item: staged while warp 0 waits
+        const float amin = s > 0 ? tile_stage_sa<HY>(w.t[0], c, l, it.x0, it.y0, smt, NDH) : 0.f;
         __syncthreads();
         if (PP) {
             // one code copy for both hemispheres: the stencils and weights come from the table
             if (s == 0) boundary_item<NDH>(w.t[h], c, l, tile, it.x0, it.y0, w.bc);
-            else tile_item<NDH, true, true, HY>(w.t[0], c, l, tile, it.x0, it.y0, smt,
-                                                w.st + ((size_t)k * 2 + h) * NDH, sts);
+            else tile_item<NDH, true, true, HY, true>(w.t[0], c, l, tile, it.x0, it.y0, smt,
+                                                      w.st + ((size_t)k * 2 + h) * NDH, sts, amin);
         } else if (h == 0) {
             // one inlined copy per hemisphere keeps every per-direction constant a static operand
             if (s == 0) boundary_item<NDH>(w.t[0], c, l, tile, it.x0, it.y0, w.bc);
-            else tile_item<NDH, true, false, HY>(w.t[0], c, l, tile, it.x0, it.y0, smt, nullptr,
-                                                 nullptr);
+            else tile_item<NDH, true, false, HY, true>(w.t[0], c, l, tile, it.x0, it.y0, smt,
+                                                       nullptr, nullptr, amin);
         } else {
             if (s == 0) boundary_item<NDH>(w.t[1], c, l, tile, it.x0, it.y0, w.bc);
-            else tile_item<NDH, true, false, HY>(w.t[1], c, l, tile, it.x0, it.y0, smt, nullptr,
-                                                 nullptr);
+            else tile_item<NDH, true, false, HY, true>(w.t[1], c, l, tile, it.x0, it.y0, smt,
+                                                       nullptr, nullptr, amin);
         }
         // every thread read `cur` before the dependency barrier above, so the next item can be
         // published now, by the barrier that also ends this one
