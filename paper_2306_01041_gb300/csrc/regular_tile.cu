@@ -205,6 +205,20 @@ __device__ __forceinline__ void tile_item(const TileArgs &a, const PlaneCtx &c, 
     // stage the upwind plane (every direction's intensity, and S with alpha), with halo; slot x
     // of SA holds (S, alpha) at x and x + 1.  A float4 never straddles the periodic seam because
     // nx and x0 - TL_HXP are multiples of 4.  amin: smallest upwind alpha this thread staged.
+    // the item's own points: S and alpha on plane k, loaded before the staging (latency overlap)
+    int gxy[TL_PPT], slot[TL_PPT];
+    float Sk[TL_PPT], ak[TL_PPT], jacc[TL_PPT];
+    bool ok[TL_PPT];
+#pragma unroll
+    for (int m = 0; m < TL_PPT; ++m) {   // rows 2 ly and 2 ly + 1 of the tile
+        const int x = x0 + lx, y = y0 + TL_PPT * ly + m;
+        ok[m] = x < a.nx && y < a.ny;
+        gxy[m] = ok[m] ? y * a.nx + x : 0;
+        slot[m] = (TL_PPT * ly + m + hy) * TL_PW + lx + TL_HXP;
+        Sk[m] = ok[m] ? __ldg(Sl + (size_t)c.k * a.np + gxy[m]) : 0.f;
+        ak[m] = ok[m] ? __ldg(al + (size_t)c.k * a.np + gxy[m]) : 0.f;
+        jacc[m] = 0.f;
+    }
     if (PP && tid < NDH * 8)
         reinterpret_cast<int *>(sts)[tid] = __ldg(reinterpret_cast<const int *>(gst) + tid);
     const float hds_min = PP ? __ldg(&gst->hds_min) : a.hds_min;
@@ -251,20 +265,6 @@ __device__ __forceinline__ void tile_item(const TileArgs &a, const PlaneCtx &c, 
     // the 1e-4 margin covers the rounding of the interpolated alpha, so that an interval the
     // general path would send to the series never takes the exact formula
     const bool thick = __syncthreads_and(amin * hds_min >= 0.1f * 1.0001f);
-    // the item's own points: S and alpha on plane k
-    int gxy[TL_PPT], slot[TL_PPT];
-    float Sk[TL_PPT], ak[TL_PPT], jacc[TL_PPT];
-    bool ok[TL_PPT];
-#pragma unroll
-    for (int m = 0; m < TL_PPT; ++m) {   // rows 2 ly and 2 ly + 1 of the tile
-        const int x = x0 + lx, y = y0 + TL_PPT * ly + m;
-        ok[m] = x < a.nx && y < a.ny;
-        gxy[m] = ok[m] ? y * a.nx + x : 0;
-        slot[m] = (TL_PPT * ly + m + hy) * TL_PW + lx + TL_HXP;
-        Sk[m] = ok[m] ? __ldg(Sl + (size_t)c.k * a.np + gxy[m]) : 0.f;
-        ak[m] = ok[m] ? __ldg(al + (size_t)c.k * a.np + gxy[m]) : 0.f;
-        jacc[m] = 0.f;
-    }
     float *In;
     size_t dstride, mstride;
     if (WAVE) {
