@@ -110,3 +110,22 @@ def test_launch_counter_without_gpu(librt):
     with pytest.raises(rt.RTError):
         rt.Batch([], 4)
     assert rt.kernel_launches() == a
+
+
+def test_accelerated_and_synthesis_entry_points_reject_bad_arguments_on_host(librt):
+    """Null handles and out-of-range knobs come back as RT_EINVAL before any device work."""
+    import paper_2306_01041_gb300 as rt
+    from paper_2306_01041_gb300 import _lib as L
+    lib = rt.lib()
+    n0 = rt.kernel_launches()
+    assert lib.rt_lambda_star(None, 4, None, 0, None, None) == L.RT_EINVAL
+    assert lib.rt_statistical_equilibrium_ali(None, None, None, None, None, None, None, None, 1,
+                                              None) == L.RT_EINVAL
+    it = ctypes.c_int(0)
+    assert lib.rt_lambda_iterate_ali(None, None, None, None, 10, 1e-3, ctypes.byref(it), None, 0,
+                                     -1, 1, None) == L.RT_EINVAL
+    assert b"newton" in lib.rt_last_error()
+    h = ctypes.c_void_p()
+    assert lib.rt_idw_create(None, None, ctypes.byref(h)) == L.RT_EINVAL
+    assert lib.rt_idw_interpolate(None, 3, None, None, None) == L.RT_EINVAL
+    assert rt.kernel_launches() == n0
