@@ -534,13 +534,14 @@ def run_iterate(args):
                    for k in ("T", "rho", "ne", "nH")])
     fn = rt.lambda_iterate_ali if args.iterate == "ali" else rt.lambda_iterate
     pops = rt.lte_populations(g, A, M)
-    fn(g, A, M, pops, max_iter=1, tol=args.tol)              # first-call set-up, untimed
+    fn(g, A, M, pops, max_iter=1, tol=args.tol, ng_period=args.ng)   # first-call set-up, untimed
     pops = rt.lte_populations(g, A, M)
     torch.cuda.synchronize()
     t = time.perf_counter()
-    it, hist, conv = fn(g, A, M, pops, max_iter=args.max_iter, tol=args.tol)
+    it, hist, conv = fn(g, A, M, pops, max_iter=args.max_iter, tol=args.tol, ng_period=args.ng)
     dt = time.perf_counter() - t
-    print(json.dumps({"workload": f"{args.iterate} iteration, regular grid {NX}x{NY}x{NZ}, "
+    ng = f", Ng every {args.ng}" if args.ng else ""
+    print(json.dumps({"workload": f"{args.iterate} iteration{ng}, regular grid {NX}x{NY}x{NZ}, "
                                   f"{len(data['lam'])} wavelengths", "iterations": it,
                       "converged": bool(conv), "seconds": round(dt, 4),
                       "ms_per_iteration": round(dt / it * 1e3, 3),
@@ -651,13 +652,15 @@ def convergence_times(torch, rt, dev, vgrid, vatom, vatm):
                    for k in ("T", "rho", "ne", "nH")])
     for name, (G, AA, MM) in (("regular_128^3", (g, A, M)),
                               ("voronoi_%d_sites" % vgrid.npt, (vgrid, vatom, vatm[0]))):
-        for method, fn in (("lambda", rt.lambda_iterate), ("ali", rt.lambda_iterate_ali)):
+        for method, fn, ngp in (("lambda", rt.lambda_iterate, 0), ("ali", rt.lambda_iterate_ali, 0),
+                                ("lambda_ng", rt.lambda_iterate, 3),
+                                ("ali_ng", rt.lambda_iterate_ali, 3)):
             pops = rt.lte_populations(G, AA, MM)
-            fn(G, AA, MM, pops, max_iter=1, tol=1e-3)        # first-call set-up, untimed
+            fn(G, AA, MM, pops, max_iter=1, tol=1e-3, ng_period=ngp)   # first-call set-up
             pops = rt.lte_populations(G, AA, MM)
             torch.cuda.synchronize()
             t = time.perf_counter()
-            it, hist, conv = fn(G, AA, MM, pops, max_iter=300, tol=1e-3)
+            it, hist, conv = fn(G, AA, MM, pops, max_iter=300, tol=1e-3, ng_period=ngp)
             dt = time.perf_counter() - t
             res[f"{name}_{method}"] = {"iterations": it, "converged": bool(conv),
                                        "seconds": round(dt, 3), "s_per_iteration": round(dt / it, 5),
@@ -716,6 +719,7 @@ def main():
     ap.add_argument("--iterate", choices=["lambda", "ali"], default=None,
                     help="time the Lambda iteration or the accelerated one to convergence")
     ap.add_argument("--max-iter", type=int, default=300)
+    ap.add_argument("--ng", type=int, default=0, help="Ng extrapolation period (0: off)")
     ap.add_argument("--tol", type=float, default=1e-3)
     ap.add_argument("--z-stretch", type=float, default=0.0,
                     help="non-uniform z spacing amplitude a in [0, 1) (cell heights (1 -+ a) dz)")

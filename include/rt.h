@@ -208,6 +208,27 @@ rt_status rt_lambda_iterate_ali(rt_grid_t grid, const rt_atom *atom, const rt_at
                                 float *history, int use_graph, int newton, int fixed_lstar,
                                 void *stream);
 
+/* ---- Ng acceleration (not in the paper) -------------------------------------------------------
+ * A least-squares extrapolation of a fixed-point iteration from its last four iterates x0 (newest)
+ * .. x3: with d0 = x0 - x1, d1 = x1 - x2, d2 = x2 - x3, (a, b) minimise the norm of
+ * d0 - a (d0 - d1) - b (d0 - d2) weighted by 1/x0^2, and x = (1 - a - b) x0 + a x1 + b x2; exact
+ * when the error spans two eigenvectors of the iteration. */
+
+/* x0..x3, out: device float [n]; scratch: 64 bytes of device memory; *ok (host) = 1 if out was
+ * written with every entry positive (else out is unspecified: keep x0).  Synchronises on
+ * stream. */
+rt_status rt_ng_extrapolate(int64_t n, const float *x0, const float *x1, const float *x2,
+                            const float *x3, float *out, void *scratch, int *ok, void *stream);
+
+/* The Lambda iteration with every option: newton = -1 plain, 0..16 accelerated (as
+ * rt_lambda_iterate_ali, with fixed_lstar); ng_period > 0 applies the Ng extrapolation to the
+ * populations after every ng_period-th iteration from the fourth on (kept only if every
+ * population stays positive); 0 never.  Other arguments as rt_lambda_iterate. */
+rt_status rt_lambda_iterate_ex(rt_grid_t grid, const rt_atom *atom, const rt_atmos *atm,
+                               float *pops, int max_iter, double tol, int *iters_out,
+                               float *history, int use_graph, int newton, int fixed_lstar,
+                               int ng_period, void *stream);
+
 /* ---- final synthesis on a Voronoi grid (Sect. 2.5, last paragraphs) ---------------------------
  * The paper takes the emergent intensity not from the irregular grid, whose upper layers hold few
  * sites, but from the original mesh: the converged populations are interpolated to the mesh by

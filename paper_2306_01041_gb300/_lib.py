@@ -80,6 +80,10 @@ SIGNATURES = {
     "rt_lambda_iterate_ali": (c_int, [P, ctypes.POINTER(AtomDesc), ctypes.POINTER(AtmosDesc), P,
                                       c_int, c_double, ctypes.POINTER(c_int), PF, c_int, c_int,
                                       c_int, P]),
+    "rt_ng_extrapolate": (c_int, [c_int64, P, P, P, P, P, P, ctypes.POINTER(c_int), P]),
+    "rt_lambda_iterate_ex": (c_int, [P, ctypes.POINTER(AtomDesc), ctypes.POINTER(AtmosDesc), P,
+                                     c_int, c_double, ctypes.POINTER(c_int), PF, c_int, c_int,
+                                     c_int, c_int, P]),
     "rt_idw_create": (c_int, [P, P, ctypes.POINTER(P)]),
     "rt_idw_destroy": (None, [P]),
     "rt_idw_table": (c_int, [P, PI32, PF]),

@@ -241,9 +241,38 @@ def statistical_equilibrium(grid, atom: Atom, atm: Atmos, J, pops, stream=None):
     return dmax
 
 
+def _iterate_ex(grid, atom, atm, pops, max_iter, tol, use_graph, newton, fixed_lstar, ng_period,
+                stream):
+    hist = np.zeros(max_iter, np.float32)
+    it = ctypes.c_int(0)
+    st = lib().rt_lambda_iterate_ex(grid.handle, ctypes.byref(atom.desc), ctypes.byref(atm.desc),
+                                    _dev(pops, (3, grid.npt), "pops"), max_iter, float(tol),
+                                    ctypes.byref(it), hist.ctypes.data_as(L.PF), int(use_graph),
+                                    int(newton), int(bool(fixed_lstar)), int(ng_period),
+                                    _stream(stream))
+    if st not in (L.RT_OK, L.RT_ENOCONV):
+        check(st)
+    return it.value, hist[:it.value].copy(), st == L.RT_OK
+
+
+def ng_extrapolate(x0, x1, x2, x3, stream=None):
+    """Ng extrapolation of four iterates (newest first); returns (x, ok)."""
+    n = x0.numel()
+    out = torch.empty_like(x0)
+    scratch = torch.zeros(16, device=x0.device, dtype=torch.float32)
+    ok = ctypes.c_int(0)
+    check(lib().rt_ng_extrapolate(n, _dev(x0), _dev(x1), _dev(x2), _dev(x3), _dev(out),
+                                  _dev(scratch), ctypes.byref(ok), _stream(stream)))
+    return out, bool(ok.value)
+
+
 def lambda_iterate(grid, atom: Atom, atm: Atmos, pops, max_iter=300, tol=1e-3, use_graph=True,
-                   stream=None):
-    """Runs the Lambda iteration in place on pops; returns (iterations, history, converged)."""
+                   ng_period=0, stream=None):
+    """Runs the Lambda iteration in place on pops; returns (iterations, history, converged).
+    ``ng_period`` > 0: Ng extrapolation after every ng_period-th iteration."""
+    if ng_period:
+        return _iterate_ex(grid, atom, atm, pops, max_iter, tol, use_graph, -1, True, ng_period,
+                           stream)
     hist = np.zeros(max_iter, np.float32)
     it = ctypes.c_int(0)
     st = lib().rt_lambda_iterate(grid.handle, ctypes.byref(atom.desc), ctypes.byref(atm.desc),
@@ -277,9 +306,13 @@ def statistical_equilibrium_ali(grid, atom: Atom, atm: Atmos, J, Lstar, S_old, p
 
 
 def lambda_iterate_ali(grid, atom: Atom, atm: Atmos, pops, max_iter=300, tol=1e-3,
-                       use_graph=True, newton=1, fixed_lstar=True, stream=None):
+                       use_graph=True, newton=1, fixed_lstar=True, ng_period=0, stream=None):
     """Accelerated Lambda iteration in place on pops; returns (iterations, history, converged).
-    ``fixed_lstar``: Lambda* of the starting opacities held fixed (else recomputed per iteration)."""
+    ``fixed_lstar``: Lambda* of the starting opacities held fixed (else recomputed per iteration);
+    ``ng_period`` > 0: Ng extrapolation after every ng_period-th iteration."""
+    if ng_period:
+        return _iterate_ex(grid, atom, atm, pops, max_iter, tol, use_graph, newton, fixed_lstar,
+                           ng_period, stream)
     hist = np.zeros(max_iter, np.float32)
     it = ctypes.c_int(0)
     st = lib().rt_lambda_iterate_ali(grid.handle, ctypes.byref(atom.desc),

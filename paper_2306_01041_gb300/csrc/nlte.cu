@@ -851,10 +851,11 @@ rt_status rt_statistical_equilibrium_ali(rt_grid_t g, const rt_atom *atom, const
 
 // The Lambda iteration loop; newton < 0: plain, else accelerated with that many Newton steps
 // and Lambda* either from the starting opacities, held fixed (fixed_lstar), or recomputed from
-// every iteration's opacities.
+// every iteration's opacities.  ng_period > 0: Ng extrapolation from the last four iterates after
+// every ng_period-th iteration (from the fourth on), kept only if every population stays positive.
 static rt_status iterate(rt_grid_t g, const rt_atom *atom, const rt_atmos *atm, float *pops,
                          int max_iter, double tol, int *iters_out, float *history, int use_graph,
-                         int newton, int fixed_lstar, void *stream)
+                         int newton, int fixed_lstar, int ng_period, void *stream)
 {
     RT_TRY(check_atmos(g, atm, pops));
     if (max_iter < 1) return fail(RT_EINVAL, "max_iter must be >= 1");
@@ -865,11 +866,14 @@ static rt_status iterate(rt_grid_t g, const rt_atom *atom, const rt_atmos *atm, 
     // scratch 2: alpha, S, J [nlam][n] (+ Lambda* when accelerated) + dmax
     const bool ali = newton >= 0;
     const size_t nf = (ali ? 4 : 3) * (size_t)nlam * n;
+    const size_t nh = ng_period > 0 ? 5 * 3 * (size_t)n : 0;   // Ng: 4 iterates + the result
     void *p;
-    RT_TRY(scratch_get(g, 2, nf * sizeof(float) + 256, &p));
+    RT_TRY(scratch_get(g, 2, (nf + nh) * sizeof(float) + 256, &p));
     float *alpha = (float *)p, *S = alpha + (size_t)nlam * n, *J = S + (size_t)nlam * n;
     float *L = ali ? J + (size_t)nlam * n : nullptr;
-    float *dmax = (float *)p + nf;
+    float *hist = (float *)p + nf;                 // [5][3 n]
+    float *dmax = (float *)p + nf + nh;
+    void *ngs = (void *)((((uintptr_t)dmax + 16) + 63) & ~(uintptr_t)63);   // 64 B, in the pad
     if (ali) RT_TRY(lambda_star_prepare(g));
     dmax = (float *)(((uintptr_t)dmax + 15) & ~(uintptr_t)15);
     float *h_dmax = nullptr;
@@ -962,6 +966,23 @@ static rt_status iterate(rt_grid_t g, const rt_atom *atom, const rt_atmos *atm, 
             result = RT_OK;
             break;
         }
+        if (ng_period > 0) {
+            const size_t m = 3 * (size_t)n;
+            float *H[4];
+            for (int q = 0; q < 4; ++q) H[q] = hist + (size_t)((it - q) & 3) * m;
+            RT_CUDA(cudaMemcpyAsync(H[0], pops, m * sizeof(float), cudaMemcpyDeviceToDevice, st));
+            if (it >= 4 && it % ng_period == 0) {
+                int ok = 0;
+                float *out = hist + 4 * m;
+                RT_TRY(ng_extrapolate(H[0], H[1], H[2], H[3], (int64_t)m, out, ngs, st, &ok));
+                if (ok) {
+                    RT_CUDA(cudaMemcpyAsync(pops, out, m * sizeof(float), cudaMemcpyDeviceToDevice,
+                                            st));
+                    RT_CUDA(cudaMemcpyAsync(H[0], out, m * sizeof(float),
+                                            cudaMemcpyDeviceToDevice, st));
+                }
+            }
+        }
     }
     if (iters_out) *iters_out = std::min(it, max_iter);
     if (result == RT_ENOCONV) fail(RT_ENOCONV, "max_iter reached before the tolerance");
@@ -974,7 +995,7 @@ rt_status rt_lambda_iterate(rt_grid_t g, const rt_atom *atom, const rt_atmos *at
                             int max_iter, double tol, int *iters_out, float *history,
                             int use_graph, void *stream)
 {
-    return iterate(g, atom, atm, pops, max_iter, tol, iters_out, history, use_graph, -1, 0,
+    return iterate(g, atom, atm, pops, max_iter, tol, iters_out, history, use_graph, -1, 0, 0,
                    stream);
 }
 
@@ -987,7 +1008,20 @@ rt_status rt_lambda_iterate_ali(rt_grid_t g, const rt_atom *atom, const rt_atmos
     if (atom && atom->nlam > 64)
         return fail(RT_EINVAL, "the accelerated update takes at most 64 wavelengths");
     return iterate(g, atom, atm, pops, max_iter, tol, iters_out, history, use_graph, newton,
-                   fixed_lstar, stream);
+                   fixed_lstar, 0, stream);
+}
+
+rt_status rt_lambda_iterate_ex(rt_grid_t g, const rt_atom *atom, const rt_atmos *atm,
+                               float *pops, int max_iter, double tol, int *iters_out,
+                               float *history, int use_graph, int newton, int fixed_lstar,
+                               int ng_period, void *stream)
+{
+    if (newton < -1 || newton > 16) return fail(RT_EINVAL, "newton must be in -1..16");
+    if (ng_period < 0) return fail(RT_EINVAL, "ng_period must be >= 0");
+    if (newton >= 0 && atom && atom->nlam > 64)
+        return fail(RT_EINVAL, "the accelerated update takes at most 64 wavelengths");
+    return iterate(g, atom, atm, pops, max_iter, tol, iters_out, history, use_graph, newton,
+                   fixed_lstar, ng_period, stream);
 }
 
 // Host evaluation of the device Voigt function for testing: H(a, v) in FP32 arithmetic is not

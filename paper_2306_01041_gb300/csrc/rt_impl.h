@@ -155,6 +155,10 @@ rt_status voronoi_prepare(rt_grid *g, int nlam);
 rt_status lambda_star(rt_grid *g, int nlam, const float *alpha, int bc, float *L, cudaStream_t st);
 // allocates what lambda_star needs on first use (call outside stream capture)
 rt_status lambda_star_prepare(rt_grid *g);
+// Ng extrapolation of four iterates into out (n floats); *ok = 1 if written with every entry
+// positive.  scratch: 64 bytes of device memory.  Synchronises on st.
+rt_status ng_extrapolate(const float *x0, const float *x1, const float *x2, const float *x3,
+                         int64_t n, float *out, void *scratch, cudaStream_t st, int *ok);
 // builds and uploads the wavefront sweep's per-plane stencil table (no-op where it cannot apply)
 rt_status regular_wave_prepare(rt_grid *g, cudaStream_t st);
 rt_status regular_emergent(rt_grid *g, const double *dir, int nlam, const float *alpha,

@@ -1,0 +1,70 @@
+"""GPU parity of the Ng extrapolation against the oracle, and the Ng-accelerated iterations
+reaching the Lambda iteration's fixed point in fewer iterations (both the plain and the
+accelerated Lambda iteration), through the C ABI."""
+import functools
+
+import numpy as np
+import pytest
+
+from helpers import assert_parity, to_gpu
+from oracle.ng import ng_extrapolate as orc_ng
+from oracle.physics import Atom
+from oracle.solve import RegularGrid as OrcRegular
+from oracle.solve import lambda_iterate as orc_lambda_iterate
+from synth import make_atmosphere, model_atom, s4_quadrature
+from synth.atmosphere import regular_fields
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rt():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2306_01041_gb300 as rt
+    return rt
+
+
+def test_ng_extrapolation_matches_oracle(rt):
+    rng = np.random.default_rng(7)
+    n = 100_003
+    Q = rng.normal(size=(n, 2))
+    xstar = 1.0 + rng.random(n)
+    c = rng.normal(size=2)
+    # error in a two-dimensional subspace, eigenvalues 0.9 and -0.5
+    xs = [xstar + Q @ (c * np.array([0.9, -0.5]) ** k) * 0.1 for k in range(4)]
+    xs32 = [x.astype(np.float32) for x in xs]
+    ref = orc_ng(*[x.astype(np.float64) for x in xs32[::-1]])
+    got, ok = rt.ng_extrapolate(*[to_gpu(x) for x in xs32[::-1]])
+    assert ok
+    assert_parity(got.cpu().numpy(), ref, rel=1e-5, floor=0.0, what="Ng extrapolation")
+    assert_parity(got.cpu().numpy(), xstar, rel=1e-4, floor=0.0, what="Ng vs fixed point")
+
+
+@functools.lru_cache(maxsize=None)
+def _setup(nx, ny, nz):
+    atm = make_atmosphere(0)
+    f, ax = regular_fields(nx, ny, nz, atm)
+    data = model_atom(np.min(f["ne"] / np.sqrt(f["T"])))
+    return atm, f, ax, data
+
+
+@pytest.mark.parametrize("method", ["lambda", "ali"])
+def test_ng_accelerated_iterations_reach_the_fixed_point(rt, method):
+    nx, ny, nz = 20, 20, 32
+    atm, f, (x, y, z, dx, dy), data = _setup(nx, ny, nz)
+    dirs, w = s4_quadrature()
+    A = Atom(data, atm.kappa0)
+    fixed, _, _ = orc_lambda_iterate(OrcRegular(nx, ny, nz, dx, dy, z, dirs, w), A, f["T"],
+                                     f["rho"], f["ne"], f["nH"], max_iter=300, tol=1e-7)
+    g = rt.RegularGrid(nx, ny, nz, dx, dy, z, dirs, w)
+    ga = rt.Atom(data, atm.kappa0)
+    gm = rt.Atmos(to_gpu(f["T"]), to_gpu(f["rho"]), to_gpu(f["ne"]), to_gpu(f["nH"]))
+    fn = rt.lambda_iterate if method == "lambda" else rt.lambda_iterate_ali
+    p0 = rt.lte_populations(g, ga, gm)
+    it0, _, c0 = fn(g, ga, gm, p0, max_iter=300, tol=1e-4)
+    p1 = rt.lte_populations(g, ga, gm)
+    it1, _, c1 = fn(g, ga, gm, p1, max_iter=300, tol=1e-4, ng_period=3)
+    assert c0 and c1 and it1 < it0, (it1, it0)
+    assert_parity(p1.cpu().numpy(), fixed, rel=2e-3, floor=0.0, what=f"{method} + Ng fixed point")
