@@ -122,7 +122,10 @@ rt_status rt_formal_solution(rt_grid_t grid, int nlam, const float *alpha, const
  * C_ip = q n_e T^-1/2 exp(-E_ip/kT) (their inverses by detailed balance), and a grey background
  * alpha_bg = kappa0 rho (T/5000)^9 with source function B.  Wavelength nodes lam[nlam] (m) with
  * quadrature weights wlam[nlam] (m); kind[j] = 0 for a line node, 1 for the bound-free node of
- * level 1, 2 for that of level 2 (each node feeds the rate integral of its kind). */
+ * level 1, 2 for that of level 2 (each node feeds the rate integral of its kind).
+ * The atom's derived constants are held in constant memory, one copy per device, and uploaded
+ * (synchronously) by a call whose atom differs from the previous call's on that device: calls
+ * with different atoms must not overlap on the GPU. */
 typedef struct {
     double E_cm[3];           /* level energies, cm^-1 (the third is the continuum edge) */
     double g[3];              /* statistical weights */

@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "device_common.cuh"
@@ -667,16 +668,26 @@ __global__ void lte_source_adjoint_kernel(int64_t npt, const float *T, const flo
 }
 
 // ---- host side ------------------------------------------------------------------------------------
+// The atom's constants live in __constant__ memory, one copy per device: uploaded when the atom
+// differs from the last one uploaded to the current device (per-device cache under a mutex, so
+// host threads and devices do not mix).
+constexpr int MAX_DEVICES = 64;
+
 static rt_status load_atom(const rt_atom *at)
 {
+    static std::mutex mu;
     static std::vector<float> gpoly;
-    static bool gp_done = false;
+    static bool gp_done[MAX_DEVICES] = {};
     if (!at || !at->lam || !at->wlam || !at->kind) return fail(RT_EINVAL, "incomplete atom");
     if (at->nlam < 1 || at->nlam > MAX_LAM) return fail(RT_EINVAL, "atom nlam must be 1..128");
-    if (!gp_done) {
-        build_gpoly(gpoly);
-        gp_done = true;
+    int dev = 0;
+    RT_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= MAX_DEVICES) return fail(RT_EINVAL, "device index beyond 63");
+    std::lock_guard<std::mutex> lock(mu);
+    if (!gp_done[dev]) {
+        if (gpoly.empty()) build_gpoly(gpoly);
         RT_CUDA(cudaMemcpyToSymbol(c_gpoly, gpoly.data(), gpoly.size() * sizeof(float)));
+        gp_done[dev] = true;
     }
     AtomDev A;
     std::memset(&A, 0, sizeof(A));
@@ -723,13 +734,14 @@ static rt_status load_atom(const rt_atom *at)
     }
     if (nline == 0) return fail(RT_EINVAL, "atom has no line node");
     A.nline = nline;
-    // upload only when the atom changed (the copy goes through the legacy default stream)
-    static AtomDev last;
-    static bool have_last = false;
-    if (!have_last || std::memcmp(&last, &A, sizeof(A)) != 0) {
+    // upload only when the atom changed on this device (the copy goes through the legacy default
+    // stream and is synchronous)
+    static AtomDev last[MAX_DEVICES];
+    static bool have_last[MAX_DEVICES] = {};
+    if (!have_last[dev] || std::memcmp(&last[dev], &A, sizeof(A)) != 0) {
         RT_CUDA(cudaMemcpyToSymbol(c_atom, &A, sizeof(A)));
-        last = A;
-        have_last = true;
+        last[dev] = A;
+        have_last[dev] = true;
     }
     return RT_OK;
 }
