@@ -23,11 +23,19 @@ struct BatchGridDev {
     const int32_t *order;      // [ndir][n]
     const int64_t *lvl;        // level offsets, all directions concatenated
     const int32_t *lvl_base;   // [ndir + 1] start of each direction's offsets in lvl
-    const float *A, *S;        // [n][nlam] transposed inputs
+    const float2 *SA;          // [n][nlam] (S, alpha): the two are always gathered together
     float *I;                  // [ndir][n][nlam] one intensity array per direction
     float *J;                  // [n][nlam]
     int n;
 };
+
+// Floats of one grid's field block: (S, alpha) pairs, J, one I per direction; rounded up to an
+// even count so that the next grid's pairs stay 8-byte aligned.
+static inline size_t batch_grid_floats(int64_t nsites, int nlam, int ndir)
+{
+    const size_t m = (size_t)nsites * nlam;
+    return ((3 + (size_t)ndir) * m + 1) & ~(size_t)1;
+}
 
 struct BatchItem {
     int grid, dir, c0, lc;
@@ -54,15 +62,17 @@ __device__ __forceinline__ VorGather vor_gather(const BatchGridDev &g, const flo
 {
     VorGather r;
     const size_t il = (size_t)i * nlam + l;
-    r.Si = __ldg(g.S + il);
-    r.Ai = __ldg(g.A + il);
+    const float2 own = __ldg(g.SA + il);
+    r.Si = own.x;
+    r.Ai = own.y;
     // a wall neighbour (k < 0) takes the site's own S and alpha; -1 (inflow wall of the sweep)
     // brings the boundary intensity S * inflow_scale (1 thermal, 0 otherwise), -2 zero
     if (u.k1 >= 0) {
         const size_t kl = (size_t)u.k1 * nlam + l;
         r.I1 = I[kl];
-        r.S1 = __ldg(g.S + kl);
-        r.A1 = __ldg(g.A + kl);
+        const float2 sa = __ldg(g.SA + kl);
+        r.S1 = sa.x;
+        r.A1 = sa.y;
     } else {
         r.S1 = r.Si;
         r.A1 = r.Ai;
@@ -71,8 +81,9 @@ __device__ __forceinline__ VorGather vor_gather(const BatchGridDev &g, const flo
     if (u.k2 >= 0 && u.w1 != 1.f) {
         const size_t kl = (size_t)u.k2 * nlam + l;
         r.I2 = I[kl];
-        r.S2 = __ldg(g.S + kl);
-        r.A2 = __ldg(g.A + kl);
+        const float2 sa = __ldg(g.SA + kl);
+        r.S2 = sa.x;
+        r.A2 = sa.y;
     } else {
         r.S2 = r.Si;
         r.A2 = r.Ai;
@@ -185,6 +196,37 @@ static void transpose_b(const float *in, float *out, int rows, int cols, cudaStr
     transpose_kernel_b<<<grid, dim3(32, 8), 0, st>>>(in, out, rows, cols);
 }
 
+// S, alpha [rows][cols] -> (S, alpha) pairs [cols][rows]
+__global__ void transpose_pair_kernel(const float *__restrict__ S, const float *__restrict__ A,
+                                      float2 *__restrict__ out, int rows, int cols)
+{
+    __shared__ float ts[32][33], ta[32][33];
+    int c = blockIdx.x * 32 + threadIdx.x;
+    int r0 = blockIdx.y * 32;
+    for (int dr = threadIdx.y; dr < 32; dr += blockDim.y) {
+        int r = r0 + dr;
+        if (r < rows && c < cols) {
+            ts[dr][threadIdx.x] = S[(size_t)r * cols + c];
+            ta[dr][threadIdx.x] = A[(size_t)r * cols + c];
+        }
+    }
+    __syncthreads();
+    int r = r0 + threadIdx.x;
+    for (int dc = threadIdx.y; dc < 32; dc += blockDim.y) {
+        int cc = blockIdx.x * 32 + dc;
+        if (r < rows && cc < cols)
+            out[(size_t)cc * rows + r] = make_float2(ts[threadIdx.x][dc], ta[threadIdx.x][dc]);
+    }
+}
+
+static void transpose_pair(const float *S, const float *A, float2 *out, int rows, int cols,
+                           cudaStream_t st)
+{
+    dim3 grid((cols + 31) / 32, (rows + 31) / 32);
+    note_launch();
+    transpose_pair_kernel<<<grid, dim3(32, 8), 0, st>>>(S, A, out, rows, cols);
+}
+
 }  // namespace rt
 
 using namespace rt;
@@ -290,7 +332,7 @@ rt_status rt_batch_create(const rt_grid_t *grids, int ngrids, int nlam, const in
         base.push_back((int32_t)lvl.size());
     }
     size_t fsz = 0;
-    for (int i = 0; i < ngrids; ++i) fsz += (3 + (size_t)b->ndir) * grids[i]->nsites * nlam;
+    for (int i = 0; i < ngrids; ++i) fsz += batch_grid_floats(grids[i]->nsites, nlam, b->ndir);
     std::vector<float> wd(b->ndir), uf(b->ndir);
     for (int d = 0; d < b->ndir; ++d) {
         wd[d] = (float)grids[0]->wdir[d];
@@ -323,12 +365,11 @@ rt_status rt_batch_create(const rt_grid_t *grids, int ngrids, int nlam, const in
         gd.order = g->vt.d_order;
         gd.lvl = b->d_lvl;
         gd.lvl_base = b->d_lvl_base + base_at[i];
-        gd.A = f;
-        gd.S = f + m;
+        gd.SA = reinterpret_cast<const float2 *>(f);
         gd.J = f + 2 * m;
         gd.I = f + 3 * m;
         gd.n = (int)g->nsites;
-        f += (3 + (size_t)b->ndir) * m;
+        f += batch_grid_floats(g->nsites, nlam, b->ndir);
         b->h_grids.push_back(gd);
     }
     BT(cudaMemcpy(b->d_items, b->h_items.data(), b->h_items.size() * sizeof(BatchItem),
@@ -362,8 +403,7 @@ rt_status rt_batch_formal_solution(rt_batch_t b, const float *const *alpha, cons
     for (int i = 0; i < ng; ++i) {
         if (!alpha[i] || !S[i] || !J[i]) return fail(RT_EINVAL, "null field");
         const BatchGridDev &g = b->h_grids[i];
-        transpose_b(alpha[i], const_cast<float *>(g.A), b->nlam, g.n, st);
-        transpose_b(S[i], const_cast<float *>(g.S), b->nlam, g.n, st);
+        transpose_pair(S[i], alpha[i], const_cast<float2 *>(g.SA), b->nlam, g.n, st);
     }
     RT_CUDA(cudaMemsetAsync(b->d_queue, 0, sizeof(int), st));
     BatchArgs a;
