@@ -47,6 +47,8 @@ def _get():
             lib.orc_sc_regular.argtypes = [ctypes.c_int] * 3 + [ctypes.c_double] * 2 + [
                 _d, ctypes.c_int, ctypes.c_int, _d, _d, ctypes.c_int, _d, _d, ctypes.c_int, _d,
                 _d, _d]
+            lib.orc_sc_regular_face.argtypes = [ctypes.c_int] * 3 + [ctypes.c_double] * 2 + [
+                _d, ctypes.c_int, _d, _d, ctypes.c_int, _d, _d, ctypes.c_int, _d, _d, _d]
             lib.orc_sc_regular_adjoint.argtypes = [ctypes.c_int] * 3 + [ctypes.c_double] * 2 + [
                 _d, ctypes.c_int, _d, ctypes.c_int, _d, _d, ctypes.c_int, _d, _d, _d]
             lib.orc_voronoi_tables.argtypes = [ctypes.c_int64, _d, _i64, _i32, _i8, _d,
@@ -102,6 +104,27 @@ def sc_regular(nx, ny, nz, dx, dy, z, dirs, wdir, alpha, S, bc=0, ibc=None, peri
                                _p(wdir), nlam, _p(alpha), _p(S), bc, _p(ibc), _p(J), _p(I))
     if rc:
         raise MemoryError("oracle allocation failed")
+    return (J, I) if want_I else J
+
+
+def sc_regular_face(nx, ny, nz, dx, dy, z, dirs, wdir, alpha, S, bc=0, ibc=None, want_I=False):
+    """Regular-grid formal solution by face-hitting short characteristics (periodic x, y).
+    alpha, S: [nlam][npt].  Returns J (and I[ndir][nlam][npt])."""
+    alpha = _f64(alpha)
+    S = _f64(S)
+    nlam = alpha.shape[0]
+    npt = nx * ny * nz
+    assert alpha.shape == (nlam, npt) and S.shape == (nlam, npt)
+    dirs = _f64(dirs)
+    wdir = _f64(wdir)
+    ndir = len(dirs)
+    J = np.empty((nlam, npt))
+    I = np.empty((ndir, nlam, npt)) if want_I else None
+    ibc = None if ibc is None else _f64(ibc)
+    rc = _get().orc_sc_regular_face(nx, ny, nz, dx, dy, _p(_f64(z)), ndir, _p(dirs), _p(wdir),
+                                    nlam, _p(alpha), _p(S), bc, _p(ibc), _p(J), _p(I))
+    if rc:
+        raise RuntimeError("oracle: allocation failed or a plane system is singular")
     return (J, I) if want_I else J
 
 

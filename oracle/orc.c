@@ -236,6 +236,244 @@ int orc_sc_regular_adjoint(int nx, int ny, int nz, double dx, double dy, const d
 }
 
 /* ---------------------------------------------------------------------------------------
+ * Regular grid: face-hitting short characteristics (Kunasz & Auer 1988, the scheme Sect. 2.6
+ * names for the regular-grid solver).  The ray through a point of plane k is followed upwind
+ * to the first face of the grid cell it enters:
+ *   - the plane face (the previous plane of the sweep) when dz/|mu_z| <= dx/|mu_x| and
+ *     dz/|mu_z| <= dy/|mu_y|: the upwind point lies within one cell of the point's column and
+ *     I, S, alpha are bilinearly interpolated there in that plane;
+ *   - otherwise the vertical face x = x_i - sx dx (when dx/|mu_x| <= dy/|mu_y|), else
+ *     y = y_j - sy dy: I, S, alpha are bilinearly interpolated on that face between its two grid
+ *     lines (j and j - sy, or i and i - sx) and the two planes k and k -/+ 1.
+ * Segment length t = the distance to that face; delta tau = (alpha_up + alpha) / 2 * t; S
+ * linear across the interval (Eq. 2).  Periodic in x and y.
+ *
+ * On a vertical face two of the four corners lie in plane k itself, so the intensities of the
+ * plane depend on one another along the face-normal axis a, around the periodic box.  In sweep
+ * order a_0, a_1, ..., a_{n-1} (the line before a_0 is a_{n-1}) each line x_m of intensities
+ * over the other axis b obeys x_m = C_m x_{m-1} + r_m, with C_m the weights of the two corners
+ * in plane k times e^-dtau and r_m all the rest.  Composing the n steps gives
+ * x_{n-1} = P x_{n-1} + q; (1 - P) x_{n-1} = q is solved by Gaussian elimination with partial
+ * pivoting, and one more pass along a yields every line.
+ * ------------------------------------------------------------------------------------- */
+
+/* A x = b for a dense n x n row-major A (overwritten); b becomes x.  -1 if singular. */
+static int gauss_solve(int n, double *A, double *b)
+{
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (fabs(A[(size_t)r * n + c]) > fabs(A[(size_t)piv * n + c])) piv = r;
+        if (A[(size_t)piv * n + c] == 0.0) return -1;
+        if (piv != c) {
+            for (int k = 0; k < n; ++k) {
+                double t = A[(size_t)c * n + k];
+                A[(size_t)c * n + k] = A[(size_t)piv * n + k];
+                A[(size_t)piv * n + k] = t;
+            }
+            double t = b[c];
+            b[c] = b[piv];
+            b[piv] = t;
+        }
+        for (int r = c + 1; r < n; ++r) {
+            double f = A[(size_t)r * n + c] / A[(size_t)c * n + c];
+            for (int k = c; k < n; ++k) A[(size_t)r * n + k] -= f * A[(size_t)c * n + k];
+            b[r] -= f * b[c];
+        }
+    }
+    for (int c = n - 1; c >= 0; --c) {
+        double s = b[c];
+        for (int k = c + 1; k < n; ++k) s -= A[(size_t)c * n + k] * b[k];
+        b[c] = s / A[(size_t)c * n + c];
+    }
+    return 0;
+}
+
+/* index in a plane of the point at position a on the face-normal axis and b on the other */
+typedef struct {
+    int a_is_x, nx;
+} orc_axes;
+
+static inline int plane_index(const orc_axes *ax, int a, int b)
+{
+    return ax->a_is_x ? b * ax->nx + a : a * ax->nx + b;
+}
+
+typedef struct {
+    double *c0, *c1, *r;       /* [np] per point, indexed like the plane */
+    double *X, *X2, *A;        /* [nb][nb] */
+    double *v, *v2, *x;        /* [nb] */
+} orc_face_work;
+
+static void face_work_free(orc_face_work *w)
+{
+    free(w->c0); free(w->c1); free(w->r);
+    free(w->X); free(w->X2); free(w->A);
+    free(w->v); free(w->v2); free(w->x);
+}
+
+static int face_work_alloc(orc_face_work *w, int np, int nbmax)
+{
+    size_t n2 = (size_t)nbmax * nbmax;
+    w->c0 = malloc(np * sizeof(double));
+    w->c1 = malloc(np * sizeof(double));
+    w->r = malloc(np * sizeof(double));
+    w->X = malloc(n2 * sizeof(double));
+    w->X2 = malloc(n2 * sizeof(double));
+    w->A = malloc(n2 * sizeof(double));
+    w->v = malloc(nbmax * sizeof(double));
+    w->v2 = malloc(nbmax * sizeof(double));
+    w->x = malloc(nbmax * sizeof(double));
+    if (!w->c0 || !w->c1 || !w->r || !w->X || !w->X2 || !w->A || !w->v || !w->v2 || !w->x) {
+        face_work_free(w);
+        return -1;
+    }
+    return 0;
+}
+
+/* one direction, one wavelength: intensity I[npt] of the whole grid; -1 if a plane's system
+ * is singular */
+static int sc_face_one(const orc_reg *g, const double *mu, const double *al, const double *S,
+                       int bc, const double *ibc, double *I, orc_face_work *w)
+{
+    const int nx = g->nx, ny = g->ny, nz = g->nz, np = nx * ny;
+    const int up = mu[2] > 0.0;
+    const int k0 = up ? 0 : nz - 1;
+    for (int p = 0; p < np; ++p) {
+        double v;
+        if (bc == 2) v = ibc[p];
+        else if (bc == 0 && up) v = S[k0 * np + p];
+        else v = 0.0;
+        I[k0 * np + p] = v;
+    }
+    const double tx = mu[0] != 0.0 ? g->dx / fabs(mu[0]) : INFINITY;
+    const double ty = mu[1] != 0.0 ? g->dy / fabs(mu[1]) : INFINITY;
+    const int sx = mu[0] >= 0.0 ? 1 : -1, sy = mu[1] >= 0.0 ? 1 : -1;
+    for (int s = 1; s < nz; ++s) {
+        const int k = up ? s : nz - 1 - s;
+        const int ku = up ? k - 1 : k + 1;
+        const double dz = fabs(g->z[k] - g->z[ku]);
+        const double tz = dz / fabs(mu[2]);
+        double *Ik = I + (size_t)k * np;
+        const double *Iu = I + (size_t)ku * np;
+        const double *Sk = S + (size_t)k * np, *Su = S + (size_t)ku * np;
+        const double *Ak = al + (size_t)k * np, *Au = al + (size_t)ku * np;
+        if (tz <= tx && tz <= ty) {
+            /* plane face: the four corners around the upwind point in plane ku */
+            const double t = tz;
+            const double fx = t * fabs(mu[0]) / g->dx, fy = t * fabs(mu[1]) / g->dy;
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i) {
+                    const int i1 = wrap(i - sx, nx), j1 = wrap(j - sy, ny);
+                    const int c[4] = {j * nx + i, j * nx + i1, j1 * nx + i, j1 * nx + i1};
+                    const double wt[4] = {(1.0 - fx) * (1.0 - fy), fx * (1.0 - fy),
+                                          (1.0 - fx) * fy, fx * fy};
+                    double iu = 0.0, su = 0.0, au = 0.0;
+                    for (int q = 0; q < 4; ++q) {
+                        iu += wt[q] * Iu[c[q]];
+                        su += wt[q] * Su[c[q]];
+                        au += wt[q] * Au[c[q]];
+                    }
+                    const int p = j * nx + i;
+                    double ex, w0, w1;
+                    orc_linear_weights(0.5 * (au + Ak[p]) * t, &ex, &w0, &w1);
+                    Ik[p] = iu * ex + w0 * su + w1 * Sk[p];
+                }
+            continue;
+        }
+        /* vertical face, normal to axis a */
+        const orc_axes ax = {tx <= ty, nx};
+        const int na = ax.a_is_x ? nx : ny, nb = ax.a_is_x ? ny : nx;
+        const int sa = ax.a_is_x ? sx : sy, sb = ax.a_is_x ? sy : sx;
+        const double t = ax.a_is_x ? tx : ty;
+        const double fb = t * (ax.a_is_x ? fabs(mu[1]) / g->dy : fabs(mu[0]) / g->dx);
+        const double fz = t * fabs(mu[2]) / dz;
+        const double wk0 = (1.0 - fz) * (1.0 - fb), wk1 = (1.0 - fz) * fb;   /* plane k */
+        const double wu0 = fz * (1.0 - fb), wu1 = fz * fb;                   /* plane ku */
+        for (int a = 0; a < na; ++a)
+            for (int b = 0; b < nb; ++b) {
+                const int a1 = wrap(a - sa, na), b1 = wrap(b - sb, nb);
+                const int p = plane_index(&ax, a, b);
+                const int q0 = plane_index(&ax, a1, b), q1 = plane_index(&ax, a1, b1);
+                const double su = wk0 * Sk[q0] + wk1 * Sk[q1] + wu0 * Su[q0] + wu1 * Su[q1];
+                const double au = wk0 * Ak[q0] + wk1 * Ak[q1] + wu0 * Au[q0] + wu1 * Au[q1];
+                double ex, w0, w1;
+                orc_linear_weights(0.5 * (au + Ak[p]) * t, &ex, &w0, &w1);
+                w->c0[p] = ex * wk0;
+                w->c1[p] = ex * wk1;
+                w->r[p] = ex * (wu0 * Iu[q0] + wu1 * Iu[q1]) + w0 * su + w1 * Sk[p];
+            }
+        /* x_m = X_m y + v_m with y the unknown last line; X_{-1} = 1, v_{-1} = 0 */
+        for (int r = 0; r < nb; ++r) {
+            for (int c = 0; c < nb; ++c) w->X[(size_t)r * nb + c] = r == c ? 1.0 : 0.0;
+            w->v[r] = 0.0;
+        }
+        for (int m = 0; m < na; ++m) {
+            const int a = sa > 0 ? m : na - 1 - m;
+            for (int b = 0; b < nb; ++b) {
+                const int b1 = wrap(b - sb, nb), p = plane_index(&ax, a, b);
+                for (int c = 0; c < nb; ++c)
+                    w->X2[(size_t)b * nb + c] = w->c0[p] * w->X[(size_t)b * nb + c] +
+                                                w->c1[p] * w->X[(size_t)b1 * nb + c];
+                w->v2[b] = w->c0[p] * w->v[b] + w->c1[p] * w->v[b1] + w->r[p];
+            }
+            double *t1 = w->X; w->X = w->X2; w->X2 = t1;
+            double *t2 = w->v; w->v = w->v2; w->v2 = t2;
+        }
+        for (int r = 0; r < nb; ++r) {
+            for (int c = 0; c < nb; ++c)
+                w->A[(size_t)r * nb + c] = (r == c ? 1.0 : 0.0) - w->X[(size_t)r * nb + c];
+            w->x[r] = w->v[r];
+        }
+        if (gauss_solve(nb, w->A, w->x)) return -1;
+        /* the pass along a from the closed cycle: w->x holds the line before a_0 */
+        for (int m = 0; m < na; ++m) {
+            const int a = sa > 0 ? m : na - 1 - m;
+            for (int b = 0; b < nb; ++b) {
+                const int b1 = wrap(b - sb, nb), p = plane_index(&ax, a, b);
+                w->v2[b] = w->c0[p] * w->x[b] + w->c1[p] * w->x[b1] + w->r[p];
+                Ik[p] = w->v2[b];
+            }
+            double *t2 = w->x; w->x = w->v2; w->v2 = t2;
+        }
+    }
+    return 0;
+}
+
+/* J[nlam][npt] = sum_d w_d I_d; optional I_out[ndir][nlam][npt].  Periodic in x and y.
+ * Returns -1 on an allocation failure or a singular plane system. */
+int orc_sc_regular_face(int nx, int ny, int nz, double dx, double dy, const double *z, int ndir,
+                        const double *dirs, const double *wdir, int nlam, const double *alpha,
+                        const double *S, int bc, const double *ibc, double *J, double *I_out)
+{
+    orc_reg g = {nx, ny, nz, dx, dy, z, 1};
+    const size_t npt = (size_t)nx * ny * nz, nb = (size_t)nx * ny;
+    const int nbmax = nx > ny ? nx : ny;
+    int failed = 0;
+    memset(J, 0, sizeof(double) * npt * nlam);
+    for (int d = 0; d < ndir; ++d) {
+#pragma omp parallel for schedule(dynamic) reduction(| : failed)
+        for (int l = 0; l < nlam; ++l) {
+            orc_face_work w;
+            double *I = (double *)malloc(npt * sizeof(double));
+            if (!I || face_work_alloc(&w, nx * ny, nbmax)) {
+                free(I);
+                failed = 1;
+                continue;
+            }
+            if (sc_face_one(&g, dirs + 3 * d, alpha + l * npt, S + l * npt, bc,
+                            ibc ? ibc + ((size_t)d * nlam + l) * nb : NULL, I, &w))
+                failed = 1;
+            for (size_t p = 0; p < npt; ++p) J[l * npt + p] += wdir[d] * I[p];
+            if (I_out) memcpy(I_out + ((size_t)d * nlam + l) * npt, I, npt * sizeof(double));
+            face_work_free(&w);
+            free(I);
+        }
+    }
+    return failed ? -1 : 0;
+}
+
+/* ---------------------------------------------------------------------------------------
  * Voronoi grid (Sect. 2.5, Eq. 5 and the weight formula after it).
  * Upwind candidates of site i for direction u: Delaunay neighbours k whose line toward i makes
  * v = u . e(k->i) > 0 and that lie on the upwind side in height, (z_i - z_k) sign(mu_z) > 0.
