@@ -150,7 +150,7 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     atm, f, (x, y, z, dx, dy), data, dirs, w = setup_problem(torch, dev, args.z_stretch)
-    g = rt.RegularGrid(NX, NY, NZ, dx, dy, z, dirs, w)
+    g = rt.RegularGrid(NX, NY, NZ, dx, dy, z, dirs, w, scheme=args.scheme)
     atom = rt.Atom(data, atm.kappa0)
     nlam = atom.nlam
     npt = NX * NY * NZ
@@ -241,14 +241,17 @@ def run_gpu(args):
     # path does not apply, one launch per plane step and hemisphere (sc_tile_kernel) plus the two
     # boundary planes; the achieved rate is the interior updates over the graph's event time
     interior_flops = FLOP_PER_UPDATE * NX * NY * (NZ - 1) * NDIR * nlam
-    if launches[1] == 1:
+    if args.scheme == "face":
+        # face_sweep_kernel, then the fixed-order sum of the two hemispheres' J partials
+        kname, per_launch_ms = "face_sweep_kernel", fs_ms
+    elif launches[1] == 1:
         kname, per_launch_ms = "sc_wave_kernel", fs_ms
     else:
         kname, per_launch_ms = "sc_tile_kernel", fs_ms / (2 * (NZ - 1))
     achieved = interior_flops / (fs_ms * 1e-3) / 1e12
     traffic = None
-    prof = PROFILED[kname]
-    if prof["sha1"] == kernel_hash() and prof["dram_bytes_per_launch"]:
+    prof = PROFILED.get(kname)
+    if prof and prof["sha1"] == kernel_hash() and prof["dram_bytes_per_launch"]:
         traffic = prof["dram_bytes_per_launch"]
 
     # end to end through the public API with host buffers: H2D of the step's inputs (atmosphere
@@ -721,6 +724,9 @@ def main():
     ap.add_argument("--max-iter", type=int, default=300)
     ap.add_argument("--ng", type=int, default=0, help="Ng extrapolation period (0: off)")
     ap.add_argument("--tol", type=float, default=1e-3)
+    ap.add_argument("--scheme", choices=["plane", "face"], default="plane",
+                    help="regular-grid short characteristics: plane to plane (default) or face "
+                         "hitting")
     ap.add_argument("--z-stretch", type=float, default=0.0,
                     help="non-uniform z spacing amplitude a in [0, 1) (cell heights (1 -+ a) dz)")
     args = ap.parse_args()
@@ -730,6 +736,8 @@ def main():
         WORKLOAD = WORKLOAD.replace("128x128x128", f"{NX}x{NY}x{NZ}")
     if args.z_stretch:
         WORKLOAD += f", stretched z (a = {args.z_stretch})"
+    if args.scheme == "face":
+        WORKLOAD += ", face-hitting short characteristics"
     if args.warmup < 3:
         args.warmup = 3
     if args.voronoi_batch:

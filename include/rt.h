@@ -108,6 +108,23 @@ rt_status rt_grid_tables(rt_grid_t grid, int32_t *k, float *w, float *len, int32
 /* Emergent-layer point indices (host array of ntop entries). */
 rt_status rt_grid_top_points(rt_grid_t grid, int64_t *idx);
 
+/* Short-characteristics scheme of a regular grid (Sect. 2.6 cites Kunasz & Auer 1988 for it):
+ *   RT_SC_PLANE (default): plane to plane -- the upwind point of a point of plane k is where the
+ *     ray crosses the previous plane of the sweep, however far from the point's column;
+ *   RT_SC_FACE: face hitting -- the upwind point is on the first face of the cell the ray enters:
+ *     the previous plane when dz/|mu_z| <= dx/|mu_x| and dy/|mu_y|, else the vertical face x_i -
+ *     sx dx (when dx/|mu_x| <= dy/|mu_y|) or y_j - sy dy, where I, S, alpha are bilinear between the
+ *     face's two grid lines and the planes k and k -/+ 1.  The intensities of a plane then depend on
+ *     one another around the periodic box; that cycle is closed to a relative 1e-9 of the plane's
+ *     intensities.
+ * The scheme applies to rt_formal_solution and so to the Lambda iterations; rt_lambda_star,
+ * rt_emergent_intensity and the adjoint stay plane to plane.  RT_SC_FACE needs periodic sides and
+ * nx, ny <= 256; its tables (per direction and plane) are built on first selection (synchronous).
+ * RT_EINVAL for a Voronoi grid, closed sides, larger planes, or planes so far apart that the
+ * cycle would need more than 16 laps of the box to close. */
+enum rt_sc_scheme { RT_SC_PLANE = 0, RT_SC_FACE = 1 };
+rt_status rt_grid_set_scheme(rt_grid_t grid, int scheme);
+
 /* Formal solution (Eq. 2 along every ray of the quadrature) and J = sum_d w_d I_d (Eq. 4).
  * alpha, S: [nlam][npt] device; J: [nlam][npt] device, overwritten.
  * I_bc: device [ndir][nlam][nb] when bc == RT_BC_ARRAY, else ignored.

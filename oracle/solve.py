@@ -12,12 +12,18 @@ from .physics import Atom
 
 
 class RegularGrid:
-    def __init__(self, nx, ny, nz, dx, dy, z, dirs, wdir, periodic=True):
+    """scheme: "plane" (plane-to-plane short characteristics) or "face" (face hitting, periodic
+    sides only); lambda_star is the plane-to-plane one for both."""
+
+    def __init__(self, nx, ny, nz, dx, dy, z, dirs, wdir, periodic=True, scheme="plane"):
         self.nx, self.ny, self.nz, self.dx, self.dy = nx, ny, nz, dx, dy
         self.z = np.asarray(z, float)
         self.dirs = np.asarray(dirs, float)
         self.wdir = np.asarray(wdir, float)
         self.periodic = periodic
+        if scheme not in ("plane", "face") or (scheme == "face" and not periodic):
+            raise ValueError("scheme must be 'plane', or 'face' with periodic sides")
+        self.scheme = scheme
 
     def lambda_star(self, alpha, bc=0):
         from .ali import lambda_star_regular
@@ -25,6 +31,10 @@ class RegularGrid:
                                    self.wdir, alpha, bc=bc, periodic=self.periodic)
 
     def formal_solution(self, alpha, S, bc=0, ibc=None, want_I=False):
+        if self.scheme == "face":
+            return lib.sc_regular_face(self.nx, self.ny, self.nz, self.dx, self.dy, self.z,
+                                       self.dirs, self.wdir, alpha, S, bc=bc, ibc=ibc,
+                                       want_I=want_I)
         return lib.sc_regular(self.nx, self.ny, self.nz, self.dx, self.dy, self.z, self.dirs,
                               self.wdir, alpha, S, bc=bc, ibc=ibc, periodic=self.periodic,
                               want_I=want_I)

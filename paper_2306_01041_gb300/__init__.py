@@ -4,7 +4,8 @@
 Build the library first (``python -c "import __graft_entry__ as g; g.build()"`` or
 ``python paper_2306_01041_gb300/build.py``); importing the API raises if it is missing.
 """
-from ._lib import (RT_BC_ARRAY, RT_BC_THERMAL, RT_BC_ZERO, RTError, lib)  # noqa: F401
+from ._lib import (RT_BC_ARRAY, RT_BC_THERMAL, RT_BC_ZERO, RT_SC_FACE,  # noqa: F401
+                   RT_SC_PLANE, RTError, lib)
 from .api import (IDW, Atmos, Atom, Batch, EmergentIntensity, Grid, RegularGrid,  # noqa: F401
                   VoronoiGrid, emergent_intensity, final_synthesis, formal_solution,
                   formal_solution_adjoint,

@@ -25,6 +25,7 @@ STATUS_NAMES = ["RT_OK", "RT_EINVAL", "RT_ENOMEM", "RT_ECUDA", "RT_ECYCLE", "RT_
                 "RT_ENAN", "RT_ECAPACITY", "RT_ENOCONV"]
 RT_GRID_REGULAR, RT_GRID_VORONOI = 0, 1
 RT_BC_THERMAL, RT_BC_ZERO, RT_BC_ARRAY = 0, 1, 2
+RT_SC_PLANE, RT_SC_FACE = 0, 1
 
 
 class GridDesc(ctypes.Structure):
@@ -61,6 +62,7 @@ SIGNATURES = {
     "rt_grid_info": (c_int, [P, PI64, PI64, ctypes.POINTER(c_int), PI64]),
     "rt_grid_tables": (c_int, [P, PI32, PF, PF, PI32]),
     "rt_grid_top_points": (c_int, [P, PI64]),
+    "rt_grid_set_scheme": (c_int, [P, c_int]),
     "rt_formal_solution": (c_int, [P, c_int, P, P, c_int, P, P, P, P]),
     "rt_source_terms_lte": (c_int, [c_int64, P, P, c_double, c_double, P, P, P]),
     "rt_source_terms_lte_adjoint": (c_int, [c_int64, P, P, c_double, c_double, P, P, P, P]),

@@ -64,6 +64,13 @@ class Grid:
             L._lib.rt_grid_destroy(h)
             self._h = None
 
+    def set_scheme(self, scheme):
+        """Short-characteristics scheme of a regular grid: "plane" (default) or "face"."""
+        code = {"plane": L.RT_SC_PLANE, "face": L.RT_SC_FACE}[scheme]
+        check(lib().rt_grid_set_scheme(self._h, code))
+        self.scheme = scheme
+        return self
+
     def top_points(self):
         out = np.empty(self.ntop, np.int64)
         check(lib().rt_grid_top_points(self._h, out.ctypes.data_as(L.PI64)))
@@ -89,7 +96,7 @@ def _dirs(dirs, wdir):
     return d, w
 
 
-def RegularGrid(nx, ny, nz, dx, dy, z, dirs, wdir, periodic=True) -> Grid:
+def RegularGrid(nx, ny, nz, dx, dy, z, dirs, wdir, periodic=True, scheme="plane") -> Grid:
     z = _np(z, np.float64)
     d, w = _dirs(dirs, wdir)
     desc = L.GridDesc()
@@ -104,6 +111,9 @@ def RegularGrid(nx, ny, nz, dx, dy, z, dirs, wdir, periodic=True) -> Grid:
     desc.r_exponent = 7.0
     g = Grid(desc, (z, d, w))
     g.shape = (nz, ny, nx)
+    g.scheme = "plane"
+    if scheme != "plane":
+        g.set_scheme(scheme)
     return g
 
 

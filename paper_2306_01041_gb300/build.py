@@ -12,7 +12,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "librt.so")
 SOURCES = ["api.cu", "regular.cu", "regular_tile.cu", "regular_cluster.cu", "voronoi.cu",
-           "nlte.cu", "batch.cu", "noalloc.cu", "ali.cu", "idw.cu", "ng.cu"]
+           "nlte.cu", "batch.cu", "noalloc.cu", "ali.cu", "idw.cu", "ng.cu",
+           "regular_face.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fopenmp,-O3",
          "-Xptxas", "-warn-spills"]

@@ -942,7 +942,9 @@ static rt_status iterate(rt_grid_t g, const rt_atom *atom, const rt_atmos *atm, 
         // the formal solution allocates its scratch on first use: do that before capturing
         void *q;
         const size_t ndh = std::max(g->dir_up.size(), g->dir_dn.size());
-        if (g->kind == RT_GRID_REGULAR) {
+        if (g->kind == RT_GRID_REGULAR && g->sc_face) {
+            RT_TRY(face_prepare(g, nlam));
+        } else if (g->kind == RT_GRID_REGULAR) {
             RT_TRY(scratch_get(g, 0, 2 * (size_t)nlam * ndh * g->nx * g->ny * sizeof(float), &q));
             RT_TRY(scratch_get(g, 3, regular_wave_scratch(g, nlam), &q));
         }

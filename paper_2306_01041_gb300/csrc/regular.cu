@@ -178,6 +178,7 @@ rt_status regular_formal_solution(rt_grid *g, int nlam, const float *alpha, cons
                                   cudaStream_t st)
 {
     if (nlam > 65535) return fail(RT_EINVAL, "nlam too large");
+    if (g->sc_face) return face_formal_solution(g, nlam, alpha, S, bc, I_bc, J, I_dir, st);
     if (!I_dir) {
         bool done = false;
         RT_TRY(regular_cluster_sweep(g, nlam, alpha, S, bc, J, st, &done));

@@ -1,0 +1,448 @@
+// Face-hitting short characteristics on the regular grid (Kunasz & Auer 1988, the scheme Sect. 2.6
+// names for the regular-grid solver), selected per grid by rt_grid_set_scheme(RT_SC_FACE).
+//
+// The ray through a point of plane k is followed upwind to the first face of the cell it enters.
+// If that is the plane face (dz/|mu_z| <= dx/|mu_x|, dy/|mu_y|), the upwind point lies within one
+// cell of the point's column in the previous plane of the sweep and I, S, alpha are bilinear there.
+// Otherwise it is a vertical face normal to the axis a (x when dx/|mu_x| <= dy/|mu_y|, else y), and
+// I, S, alpha are bilinear on that face between the grid lines b and b - s_b and the planes k and
+// k -/+ 1: two of the four corners lie in plane k itself, one line upwind along a.  Segment length
+// t, delta tau = (alpha_up + alpha) t / 2, S linear across the interval (Eq. 2).  Periodic in x, y.
+//
+// Work decomposition.  One block per (wavelength, group of up to 12 directions of one hemisphere),
+// one warp per direction.  A warp keeps one plane of intensities per (wavelength, direction) in
+// global memory, stored line by line along a ([a][b], b contiguous), and sweeps each plane line by
+// line in upwind order along a, the lanes across b: line a needs only line a - s_a of planes k and
+// k -/+ 1 (and, on the plane face, line a of plane k -/+ 1), staged in a two-line ring in shared
+// memory, while the next line's loads are in flight.  The plane buffer is updated in place: line a
+// of the previous plane is no longer needed once line a of this plane is computed (the ring holds
+// it for the next line).
+//
+// Vertical faces couple a plane's lines around the periodic box.  Each line's dependence on the
+// line before it has total weight (1 - f_z) e^-dtau <= 1 - f_z, f_z = t |mu_z| / dz < 1, so the walk
+// starts W lines before the first line it stores, from the previous plane's intensities, with
+// (1 - f_z)^W <= 1e-9: the stored lines then carry the periodic solution to far below FP32
+// rounding.  The plane face has no such coupling (W = 0).
+//
+// After each plane the block sums w_d I_d over its directions, in group order, into its J partial
+// (directions with a = x hold their plane transposed, so their tiles pass through shared memory);
+// a second kernel adds the partials of the other groups to J in a fixed order.
+#include <cmath>
+#include <vector>
+
+#include "device_common.cuh"
+#include "rt_impl.h"
+
+namespace rt {
+
+constexpr int FACE_MAXW = 12;        // directions (warps) per block
+constexpr int FACE_MAXNB = 256;      // largest nx, ny
+constexpr double FACE_EPS = 1e-9;    // closure truncation of the periodic plane system
+
+struct FaceDir {
+    int dir;          // index in the grid's direction list
+    int a_is_x;       // 1: lines run along x (face x = x_i - s_a dx), 0: along y
+    int sa, sb;       // upwind steps +-1 along a and b
+    int up;           // mu_z > 0
+    float w;          // quadrature weight
+};
+
+// per (direction, plane step): X_up = (1 - fb) (wA X_u[a][b] + wU X_u[a-sa][b] + wK X_k[a-sa][b])
+//                                    + fb (same at b - sb), X_u the upwind plane, X_k this plane
+struct FaceStep {
+    float t, wA, wU, wK, fb;
+    int warm;         // lines walked before the first stored one (vertical face), else 0
+};
+
+struct FaceTables {
+    FaceDir *d_dirs = nullptr;     // [ndir], grouped
+    FaceStep *d_steps = nullptr;   // [ndir][nz] by grid direction index, step s = 1 .. nz-1
+    int *d_first = nullptr;        // [ngroups + 1]
+    int ngroups = 0, wpb = 0, nbpad = 0;
+};
+
+void face_release(FaceTables *t)
+{
+    if (!t) return;
+    if (t->d_dirs) cudaFree(t->d_dirs);
+    if (t->d_steps) cudaFree(t->d_steps);
+    if (t->d_first) cudaFree(t->d_first);
+    delete t;
+}
+
+struct FaceArgs {
+    const float *alpha, *S, *I_bc;
+    float *I_dir, *J, *Jp, *buf;
+    const FaceDir *dirs;
+    const FaceStep *steps;
+    const int *first;
+    unsigned *err;
+    int nx, ny, nz, nlam, ndir, bc, nbpad;
+};
+
+enum { R_IK, R_SK, R_AK, R_IU, R_SU, R_AU };
+
+template <int MAXM>
+__global__ void __launch_bounds__(FACE_MAXW * 32, 1) face_sweep_kernel(FaceArgs a)
+{
+    extern __shared__ float sm[];
+    __shared__ FaceDir sdir[FACE_MAXW];
+    const int lam = blockIdx.x, grp = blockIdx.y;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    const int d0 = a.first[grp], nd = a.first[grp + 1] - d0;
+    if (threadIdx.x < nd) sdir[threadIdx.x] = a.dirs[d0 + threadIdx.x];
+    __syncthreads();
+    const int nx = a.nx, ny = a.ny, nz = a.nz, np = nx * ny;
+    const size_t npt = (size_t)np * nz;
+    const float *Al = a.alpha + (size_t)lam * npt, *Sl = a.S + (size_t)lam * npt;
+    const bool active = warp < nd;
+    const FaceDir D = sdir[active ? warp : 0];
+    const int up = sdir[0].up;
+    const int na = D.a_is_x ? nx : ny, nb = D.a_is_x ? ny : nx;
+    float *buf = a.buf + ((size_t)lam * a.ndir + D.dir) * np;
+    float *ring = sm + (size_t)warp * 12 * a.nbpad;
+    float *tile = sm + (size_t)wpb * 12 * a.nbpad;
+    float *Jout = (grp == 0 ? a.J : a.Jp + (size_t)(grp - 1) * a.nlam * npt) + (size_t)lam * npt;
+    float *Idir = a.I_dir ? a.I_dir + ((size_t)D.dir * a.nlam + lam) * npt : nullptr;
+    const int nbpad = a.nbpad;
+#define RING(arr, slot, b) ring[((arr) * 2 + (slot)) * nbpad + (b)]
+
+    // field index of position b on line al of plane k
+    auto fidx = [&](int k, int al, int b) -> size_t {
+        return (size_t)k * np + (D.a_is_x ? (size_t)b * nx + al : (size_t)al * nx + b);
+    };
+
+    // J partial of plane k: sum over the group's directions in group order
+    auto j_plane = [&](int k) {
+        float *Jk = Jout + (size_t)k * np;
+        for (int tj = 0; tj < ny; tj += 32)
+            for (int ti = 0; ti < nx; ti += 32) {
+                int xi = 0;
+                for (int q = 0; q < nd; ++q) {
+                    if (!sdir[q].a_is_x) continue;
+                    const float *bq = a.buf + ((size_t)lam * a.ndir + sdir[q].dir) * np;
+                    for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+                        const int r = e >> 5, c = e & 31, i = ti + r, j = tj + c;
+                        tile[(xi * 32 + r) * 33 + c] = (i < nx && j < ny) ? bq[(size_t)i * ny + j] : 0.f;
+                    }
+                    ++xi;
+                }
+                __syncthreads();
+                for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+                    const int r = e >> 5, c = e & 31, i = ti + c, j = tj + r;
+                    if (i >= nx || j >= ny) continue;
+                    float acc = 0.f;
+                    int x2 = 0;
+                    for (int q = 0; q < nd; ++q) {
+                        float v;
+                        if (sdir[q].a_is_x)
+                            v = tile[(x2++ * 32 + c) * 33 + r];
+                        else
+                            v = a.buf[((size_t)lam * a.ndir + sdir[q].dir) * np + (size_t)j * nx + i];
+                        acc = fmaf(sdir[q].w, v, acc);
+                    }
+                    if (!isfinite(acc)) flag_error(a.err, ERR_NAN);
+                    Jk[(size_t)j * nx + i] = acc;
+                }
+                __syncthreads();
+            }
+    };
+
+    // the wall plane the rays enter through
+    const int k0 = up ? 0 : nz - 1;
+    if (active) {
+        for (int m = lane; m < np; m += 32) {
+            const int al = m / nb, b = m - al * nb;
+            const size_t f = fidx(k0, al, b);
+            float v = 0.f;
+            if (a.bc == RT_BC_ARRAY)
+                v = __ldg(a.I_bc + ((size_t)D.dir * a.nlam + lam) * np + (f - (size_t)k0 * np));
+            else if (a.bc == RT_BC_THERMAL && up)
+                v = __ldg(Sl + f);
+            buf[m] = v;
+            if (Idir) Idir[f] = v;
+        }
+    }
+    __syncthreads();
+    j_plane(k0);
+
+    const int M = (nb + 31) >> 5;
+    for (int s = 1; s < nz; ++s) {
+        const int k = up ? s : nz - 1 - s, ku = up ? k - 1 : k + 1;
+        if (active) {
+            const FaceStep st = a.steps[(size_t)D.dir * nz + s];
+            // line of the m-th step of the walk (m < 0: the lines before the first stored one)
+            auto line_of = [&](int m) {
+                int r = m % na;
+                if (r < 0) r += na;
+                return D.sa > 0 ? r : na - 1 - r;
+            };
+            float pf[5][MAXM];
+            auto fetch = [&](int al) {
+#pragma unroll
+                for (int q = 0; q < MAXM; ++q) {
+                    const int b = lane + 32 * q;
+                    if (q < M && b < nb) {
+                        const size_t fk = fidx(k, al, b), fu = fidx(ku, al, b);
+                        pf[0][q] = __ldg(Sl + fk);
+                        pf[1][q] = __ldg(Al + fk);
+                        pf[2][q] = buf[(size_t)al * nb + b];
+                        pf[3][q] = __ldg(Sl + fu);
+                        pf[4][q] = __ldg(Al + fu);
+                    }
+                }
+            };
+            auto stash = [&](int slot) {
+#pragma unroll
+                for (int q = 0; q < MAXM; ++q) {
+                    const int b = lane + 32 * q;
+                    if (q < M && b < nb) {
+                        RING(R_SK, slot, b) = pf[0][q];
+                        RING(R_AK, slot, b) = pf[1][q];
+                        RING(R_IU, slot, b) = pf[2][q];
+                        RING(R_SU, slot, b) = pf[3][q];
+                        RING(R_AU, slot, b) = pf[4][q];
+                    }
+                }
+            };
+            const float g1 = st.fb, g0 = 1.f - st.fb;
+            int slot = 0;
+            int m = -st.warm - 1;
+            fetch(line_of(m));
+            stash(slot);
+            // this plane's intensity on the line before the walk: the previous plane's as a start
+            // (vertical face), unused on the plane face (wK = 0)
+#pragma unroll
+            for (int q = 0; q < MAXM; ++q) {
+                const int b = lane + 32 * q;
+                if (q < M && b < nb) RING(R_IK, slot, b) = st.wK != 0.f ? pf[2][q] : 0.f;
+            }
+            fetch(line_of(m + 1));
+            __syncwarp();
+            for (m = -st.warm; m < na; ++m) {
+                const int al = line_of(m);
+                slot ^= 1;
+                const int cur = slot, prv = slot ^ 1;
+                stash(cur);
+                if (m + 1 < na) fetch(line_of(m + 1));
+                __syncwarp();
+                const bool store = m >= 0;
+#pragma unroll
+                for (int q = 0; q < MAXM; ++q) {
+                    const int b = lane + 32 * q;
+                    if (q < M && b < nb) {
+                        const int b1 = D.sb > 0 ? (b == 0 ? nb - 1 : b - 1) : (b == nb - 1 ? 0 : b + 1);
+                        const float iu =
+                            g0 * (st.wA * RING(R_IU, cur, b) + st.wU * RING(R_IU, prv, b) +
+                                  st.wK * RING(R_IK, prv, b)) +
+                            g1 * (st.wA * RING(R_IU, cur, b1) + st.wU * RING(R_IU, prv, b1) +
+                                  st.wK * RING(R_IK, prv, b1));
+                        const float su =
+                            g0 * (st.wA * RING(R_SU, cur, b) + st.wU * RING(R_SU, prv, b) +
+                                  st.wK * RING(R_SK, prv, b)) +
+                            g1 * (st.wA * RING(R_SU, cur, b1) + st.wU * RING(R_SU, prv, b1) +
+                                  st.wK * RING(R_SK, prv, b1));
+                        const float au =
+                            g0 * (st.wA * RING(R_AU, cur, b) + st.wU * RING(R_AU, prv, b) +
+                                  st.wK * RING(R_AK, prv, b)) +
+                            g1 * (st.wA * RING(R_AU, cur, b1) + st.wU * RING(R_AU, prv, b1) +
+                                  st.wK * RING(R_AK, prv, b1));
+                        const float ak = RING(R_AK, cur, b), sk = RING(R_SK, cur, b);
+                        float ex, w0, w1;
+                        lin_weights(0.5f * (au + ak) * st.t, ex, w0, w1);
+                        const float v = fmaf(iu, ex, fmaf(w0, su, w1 * sk));
+                        RING(R_IK, cur, b) = v;
+                        if (store) {
+                            buf[(size_t)al * nb + b] = v;
+                            if (Idir) Idir[fidx(k, al, b)] = v;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        j_plane(k);
+    }
+#undef RING
+}
+
+// J += the other groups' partials, in group order
+__global__ void face_sum_kernel(float *J, const float *Jp, int nparts, size_t n)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        float v = J[i];
+        for (int p = 0; p < nparts; ++p) v += Jp[(size_t)p * n + i];
+        J[i] = v;
+    }
+}
+
+static int face_maxm(const rt_grid *g) { return std::max(g->nx, g->ny) <= 128 ? 4 : 8; }
+
+static size_t face_smem(const FaceTables *t)
+{
+    return ((size_t)t->wpb * 12 * t->nbpad + (size_t)t->wpb * 32 * 33) * sizeof(float);
+}
+
+static rt_status face_build(rt_grid *g)
+{
+    const double *z = g->z.data();
+    std::vector<FaceDir> dirs;
+    std::vector<int> first;
+    std::vector<FaceStep> steps((size_t)g->ndir * g->nz, FaceStep{0, 0, 0, 0, 0, 0});
+    int wpb = 0;
+    for (int hemi = 0; hemi < 2; ++hemi) {
+        const std::vector<int> &list = hemi == 0 ? g->dir_up : g->dir_dn;
+        for (size_t c = 0; c < list.size(); c += FACE_MAXW) {
+            first.push_back((int)dirs.size());
+            const size_t e = std::min(list.size(), c + FACE_MAXW);
+            wpb = std::max(wpb, (int)(e - c));
+            for (size_t i = c; i < e; ++i) {
+                const int q = list[i];
+                const double *u = &g->dirs[3 * q];
+                const double tx = u[0] != 0.0 ? g->dx / std::fabs(u[0]) : INFINITY;
+                const double ty = u[1] != 0.0 ? g->dy / std::fabs(u[1]) : INFINITY;
+                FaceDir d;
+                d.dir = q;
+                d.a_is_x = tx <= ty;
+                const double ua = d.a_is_x ? u[0] : u[1], ub = d.a_is_x ? u[1] : u[0];
+                const double da = d.a_is_x ? g->dx : g->dy, db = d.a_is_x ? g->dy : g->dx;
+                const int na = d.a_is_x ? g->nx : g->ny;
+                d.sa = ua >= 0.0 ? 1 : -1;
+                d.sb = ub >= 0.0 ? 1 : -1;
+                d.up = u[2] > 0.0;
+                d.w = (float)g->wdir[q];
+                dirs.push_back(d);
+                for (int s = 1; s < g->nz; ++s) {
+                    const int k = d.up ? s : g->nz - 1 - s, ku = d.up ? k - 1 : k + 1;
+                    const double dz = std::fabs(z[k] - z[ku]);
+                    const double tz = dz / std::fabs(u[2]);
+                    FaceStep &f = steps[(size_t)q * g->nz + s];
+                    if (tz <= tx && tz <= ty) {
+                        const double fa = tz * std::fabs(ua) / da;
+                        f = FaceStep{(float)tz, (float)(1.0 - fa), (float)fa, 0.f,
+                                     (float)(tz * std::fabs(ub) / db), 0};
+                    } else {
+                        const double t = d.a_is_x ? tx : ty;
+                        const double fz = t * std::fabs(u[2]) / dz;
+                        int warm = 0;
+                        if (fz < 1.0) {
+                            const double w = std::ceil(std::log(FACE_EPS) / std::log1p(-fz));
+                            if (!(w <= 16.0 * na))
+                                return fail(RT_EINVAL, "face scheme: plane spacing too coarse for "
+                                                       "the periodic closure (over 16 laps)");
+                            warm = (int)w;
+                        }
+                        f = FaceStep{(float)t, 0.f, (float)fz, (float)(1.0 - fz),
+                                     (float)(t * std::fabs(ub) / db), warm};
+                    }
+                }
+            }
+        }
+    }
+    first.push_back((int)dirs.size());
+    FaceTables *t = new FaceTables;
+    t->ngroups = (int)first.size() - 1;
+    t->wpb = wpb;
+    t->nbpad = (std::max(g->nx, g->ny) + 31) / 32 * 32;
+    cudaError_t e = cudaMalloc(&t->d_dirs, dirs.size() * sizeof(FaceDir));
+    if (e == cudaSuccess) e = cudaMalloc(&t->d_steps, steps.size() * sizeof(FaceStep));
+    if (e == cudaSuccess) e = cudaMalloc(&t->d_first, first.size() * sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(t->d_dirs, dirs.data(), dirs.size() * sizeof(FaceDir), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(t->d_steps, steps.data(), steps.size() * sizeof(FaceStep),
+                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(t->d_first, first.data(), first.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        // the largest any grid can ask of each instance, so that no grid lowers another's limit
+        const int s4 = (int)((FACE_MAXW * 12 * 128 + FACE_MAXW * 32 * 33) * sizeof(float));
+        const int s8 = (int)((FACE_MAXW * 12 * 256 + FACE_MAXW * 32 * 33) * sizeof(float));
+        e = face_maxm(g) == 4
+                ? cudaFuncSetAttribute(face_sweep_kernel<4>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, s4)
+                : cudaFuncSetAttribute(face_sweep_kernel<8>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, s8);
+    }
+    if (e != cudaSuccess) {
+        face_release(t);
+        return cuda_fail(e, "face scheme tables");
+    }
+    face_release(g->face);
+    g->face = t;
+    return RT_OK;
+}
+
+static size_t face_scratch_bytes(const rt_grid *g, int nlam)
+{
+    const size_t np = (size_t)g->nx * g->ny;
+    return ((size_t)nlam * g->ndir * np +
+            (size_t)(g->face->ngroups - 1) * nlam * np * g->nz) * sizeof(float);
+}
+
+rt_status face_prepare(rt_grid *g, int nlam)
+{
+    void *p;
+    return scratch_get(g, 4, face_scratch_bytes(g, nlam), &p);
+}
+
+rt_status face_formal_solution(rt_grid *g, int nlam, const float *alpha, const float *S, int bc,
+                               const float *I_bc, float *J, float *I_dir, cudaStream_t st)
+{
+    const FaceTables *t = g->face;
+    void *p;
+    RT_TRY(scratch_get(g, 4, face_scratch_bytes(g, nlam), &p));
+    FaceArgs a;
+    a.alpha = alpha;
+    a.S = S;
+    a.I_bc = bc == RT_BC_ARRAY ? I_bc : nullptr;
+    a.I_dir = I_dir;
+    a.J = J;
+    a.buf = (float *)p;
+    a.Jp = a.buf + (size_t)nlam * g->ndir * g->nx * g->ny;
+    a.dirs = t->d_dirs;
+    a.steps = t->d_steps;
+    a.first = t->d_first;
+    a.err = g->d_err;
+    a.nx = g->nx;
+    a.ny = g->ny;
+    a.nz = g->nz;
+    a.nlam = nlam;
+    a.ndir = g->ndir;
+    a.bc = bc;
+    a.nbpad = t->nbpad;
+    const dim3 grid((unsigned)nlam, (unsigned)t->ngroups);
+    const size_t smem = face_smem(t);
+    note_launch();
+    if (face_maxm(g) == 4)
+        face_sweep_kernel<4><<<grid, 32 * t->wpb, smem, st>>>(a);
+    else
+        face_sweep_kernel<8><<<grid, 32 * t->wpb, smem, st>>>(a);
+    RT_CUDA(cudaGetLastError());
+    if (t->ngroups > 1) {
+        note_launch();
+        face_sum_kernel<<<1216, 256, 0, st>>>(J, a.Jp, t->ngroups - 1, (size_t)nlam * g->npt);
+        RT_CUDA(cudaGetLastError());
+    }
+    return RT_OK;
+}
+
+}  // namespace rt
+
+using namespace rt;
+
+extern "C" rt_status rt_grid_set_scheme(rt_grid_t g, int scheme)
+{
+    if (!g) return fail(RT_EINVAL, "null grid");
+    if (scheme != RT_SC_PLANE && scheme != RT_SC_FACE) return fail(RT_EINVAL, "unknown scheme");
+    if (scheme == RT_SC_FACE) {
+        if (g->kind != RT_GRID_REGULAR) return fail(RT_EINVAL, "the face scheme is for regular grids");
+        if (!g->periodic) return fail(RT_EINVAL, "the face scheme needs periodic sides");
+        if (std::max(g->nx, g->ny) > FACE_MAXNB) return fail(RT_EINVAL, "face scheme: nx, ny <= 256");
+        if (!g->face) RT_TRY(face_build(g));
+    }
+    g->sc_face = scheme == RT_SC_FACE;
+    return RT_OK;
+}

@@ -83,6 +83,9 @@ struct VorTables {
     void release();
 };
 
+struct FaceTables;                             // face-hitting scheme tables (regular_face.cu)
+void face_release(FaceTables *t);
+
 struct Scratch {
     void *p = nullptr;
     size_t bytes = 0;
@@ -111,6 +114,8 @@ struct rt_grid {
     double one_dir[3] = {0, 0, 0};
     void *d_wave_st = nullptr;                 // [nz][2][12] per-plane stencils of the wavefront sweep
     std::vector<char> h_wave_st;
+    int sc_face = 0;                           // rt_grid_set_scheme(RT_SC_FACE) selected
+    rt::FaceTables *face = nullptr;
     // voronoi
     std::vector<double> xyz;
     double box[6];
@@ -130,7 +135,7 @@ struct rt_grid {
     int64_t *d_top = nullptr;
     // shared
     unsigned *d_err = nullptr;                 // device error word
-    rt::Scratch scratch[4];
+    rt::Scratch scratch[5];
     ~rt_grid();
 };
 
@@ -141,6 +146,10 @@ rt_status check_dev_error(rt_grid *g, cudaStream_t st);
 // launchers (defined in the .cu files)
 rt_status regular_formal_solution(rt_grid *g, int nlam, const float *alpha, const float *S, int bc,
                                   const float *I_bc, float *J, float *I_dir, cudaStream_t st);
+// face-hitting sweep of a grid whose scheme is RT_SC_FACE; face_prepare allocates its scratch
+rt_status face_formal_solution(rt_grid *g, int nlam, const float *alpha, const float *S, int bc,
+                               const float *I_bc, float *J, float *I_dir, cudaStream_t st);
+rt_status face_prepare(rt_grid *g, int nlam);
 // fused cluster sweep over all planes; *done = false when it does not apply to this grid
 rt_status regular_cluster_sweep(rt_grid *g, int nlam, const float *alpha, const float *S, int bc,
                                 float *J, cudaStream_t st, bool *done);
