@@ -113,7 +113,7 @@ rt_status rt_grid_top_points(rt_grid_t grid, int64_t *idx);
  *     ray crosses the previous plane of the sweep, however far from the point's column;
  *   RT_SC_FACE: face hitting -- the upwind point is on the first face of the cell the ray enters:
  *     the previous plane when dz/|mu_z| <= dx/|mu_x| and dy/|mu_y|, else the vertical face x_i -
- *     sx dx (when dx/|mu_x| <= dy/|mu_y|) or y_j - sy dy, where I, S, alpha are bilinear between the
+ *     sx dx (when dx/|mu_x| < dy/|mu_y|) or y_j - sy dy, where I, S, alpha are bilinear between the
  *     face's two grid lines and the planes k and k -/+ 1.  The intensities of a plane then depend on
  *     one another around the periodic box; that cycle is closed to a relative 1e-9 of the plane's
  *     intensities.

@@ -242,8 +242,9 @@ int orc_sc_regular_adjoint(int nx, int ny, int nz, double dx, double dy, const d
  *   - the plane face (the previous plane of the sweep) when dz/|mu_z| <= dx/|mu_x| and
  *     dz/|mu_z| <= dy/|mu_y|: the upwind point lies within one cell of the point's column and
  *     I, S, alpha are bilinearly interpolated there in that plane;
- *   - otherwise the vertical face x = x_i - sx dx (when dx/|mu_x| <= dy/|mu_y|), else
- *     y = y_j - sy dy: I, S, alpha are bilinearly interpolated on that face between its two grid
+ *   - otherwise the vertical face x = x_i - sx dx (when dx/|mu_x| < dy/|mu_y|), else
+ *     y = y_j - sy dy (on a tie the ray meets the edge the two faces share, and both give the
+ *     same upwind point): I, S, alpha are bilinearly interpolated on that face between its two grid
  *     lines (j and j - sy, or i and i - sx) and the two planes k and k -/+ 1.
  * Segment length t = the distance to that face; delta tau = (alpha_up + alpha) / 2 * t; S
  * linear across the interval (Eq. 2).  Periodic in x and y.
@@ -382,7 +383,7 @@ static int sc_face_one(const orc_reg *g, const double *mu, const double *al, con
             continue;
         }
         /* vertical face, normal to axis a */
-        const orc_axes ax = {tx <= ty, nx};
+        const orc_axes ax = {tx < ty, nx};
         const int na = ax.a_is_x ? nx : ny, nb = ax.a_is_x ? ny : nx;
         const int sa = ax.a_is_x ? sx : sy, sb = ax.a_is_x ? sy : sx;
         const double t = ax.a_is_x ? tx : ty;

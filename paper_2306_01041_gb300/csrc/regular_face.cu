@@ -4,7 +4,7 @@
 // The ray through a point of plane k is followed upwind to the first face of the cell it enters.
 // If that is the plane face (dz/|mu_z| <= dx/|mu_x|, dy/|mu_y|), the upwind point lies within one
 // cell of the point's column in the previous plane of the sweep and I, S, alpha are bilinear there.
-// Otherwise it is a vertical face normal to the axis a (x when dx/|mu_x| <= dy/|mu_y|, else y), and
+// Otherwise it is a vertical face normal to the axis a (x when dx/|mu_x| < dy/|mu_y|, else y), and
 // I, S, alpha are bilinear on that face between the grid lines b and b - s_b and the planes k and
 // k -/+ 1: two of the four corners lie in plane k itself, one line upwind along a.  Segment length
 // t, delta tau = (alpha_up + alpha) t / 2, S linear across the interval (Eq. 2).  Periodic in x, y.
@@ -14,7 +14,9 @@
 // global memory, stored line by line along a ([a][b], b contiguous), and sweeps each plane line by
 // line in upwind order along a, the lanes across b: line a needs only line a - s_a of planes k and
 // k -/+ 1 (and, on the plane face, line a of plane k -/+ 1), staged in a two-line ring in shared
-// memory, while the next line's loads are in flight.  The plane buffer is updated in place: line a
+// memory, while the next line's loads are in flight.  Directions whose lines run along x read S and
+// alpha from copies transposed to [nlam][nz][x][y] once per call, so that every line load is
+// contiguous.  The plane buffer is updated in place: line a
 // of the previous plane is no longer needed once line a of this plane is computed (the ring holds
 // it for the next line).
 //
@@ -59,6 +61,7 @@ struct FaceTables {
     FaceStep *d_steps = nullptr;   // [ndir][nz] by grid direction index, step s = 1 .. nz-1
     int *d_first = nullptr;        // [ngroups + 1]
     int ngroups = 0, wpb = 0, nbpad = 0;
+    int has_x = 0;                 // some direction's lines run along x
 };
 
 void face_release(FaceTables *t)
@@ -72,6 +75,7 @@ void face_release(FaceTables *t)
 
 struct FaceArgs {
     const float *alpha, *S, *I_bc;
+    const float *AT, *ST;          // [nlam][nz][nx][ny] transposed copies (lines along x)
     float *I_dir, *J, *Jp, *buf;
     const FaceDir *dirs;
     const FaceStep *steps;
@@ -94,11 +98,13 @@ __global__ void __launch_bounds__(FACE_MAXW * 32, 1) face_sweep_kernel(FaceArgs 
     __syncthreads();
     const int nx = a.nx, ny = a.ny, nz = a.nz, np = nx * ny;
     const size_t npt = (size_t)np * nz;
-    const float *Al = a.alpha + (size_t)lam * npt, *Sl = a.S + (size_t)lam * npt;
     const bool active = warp < nd;
     const FaceDir D = sdir[active ? warp : 0];
     const int up = sdir[0].up;
     const int na = D.a_is_x ? nx : ny, nb = D.a_is_x ? ny : nx;
+    // S and alpha with this direction's lines contiguous: [nz][na][nb]
+    const float *Sl = (D.a_is_x ? a.ST : a.S) + (size_t)lam * npt;
+    const float *Al = (D.a_is_x ? a.AT : a.alpha) + (size_t)lam * npt;
     float *buf = a.buf + ((size_t)lam * a.ndir + D.dir) * np;
     float *ring = sm + (size_t)warp * 12 * a.nbpad;
     float *tile = sm + (size_t)wpb * 12 * a.nbpad;
@@ -107,9 +113,12 @@ __global__ void __launch_bounds__(FACE_MAXW * 32, 1) face_sweep_kernel(FaceArgs 
     const int nbpad = a.nbpad;
 #define RING(arr, slot, b) ring[((arr) * 2 + (slot)) * nbpad + (b)]
 
-    // field index of position b on line al of plane k
+    // field index of position b on line al of plane k, and its index in the line-major copies
     auto fidx = [&](int k, int al, int b) -> size_t {
         return (size_t)k * np + (D.a_is_x ? (size_t)b * nx + al : (size_t)al * nx + b);
+    };
+    auto lidx = [&](int k, int al, int b) -> size_t {
+        return (size_t)k * np + (size_t)al * nb + b;
     };
 
     // J partial of plane k: sum over the group's directions in group order
@@ -158,7 +167,7 @@ __global__ void __launch_bounds__(FACE_MAXW * 32, 1) face_sweep_kernel(FaceArgs 
             if (a.bc == RT_BC_ARRAY)
                 v = __ldg(a.I_bc + ((size_t)D.dir * a.nlam + lam) * np + (f - (size_t)k0 * np));
             else if (a.bc == RT_BC_THERMAL && up)
-                v = __ldg(Sl + f);
+                v = __ldg(Sl + lidx(k0, al, b));
             buf[m] = v;
             if (Idir) Idir[f] = v;
         }
@@ -183,7 +192,7 @@ __global__ void __launch_bounds__(FACE_MAXW * 32, 1) face_sweep_kernel(FaceArgs 
                 for (int q = 0; q < MAXM; ++q) {
                     const int b = lane + 32 * q;
                     if (q < M && b < nb) {
-                        const size_t fk = fidx(k, al, b), fu = fidx(ku, al, b);
+                        const size_t fk = lidx(k, al, b), fu = lidx(ku, al, b);
                         pf[0][q] = __ldg(Sl + fk);
                         pf[1][q] = __ldg(Al + fk);
                         pf[2][q] = buf[(size_t)al * nb + b];
@@ -267,6 +276,29 @@ __global__ void __launch_bounds__(FACE_MAXW * 32, 1) face_sweep_kernel(FaceArgs 
 #undef RING
 }
 
+// in [planes][ny][nx] -> out [planes][nx][ny]
+__global__ void face_transpose_kernel(const float *__restrict__ in, float *__restrict__ out, int nx,
+                                      int ny, int nplanes)
+{
+    __shared__ float t[32][33];
+    const size_t np = (size_t)nx * ny;
+    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+    for (int p = blockIdx.z; p < nplanes; p += gridDim.z) {
+        const float *src = in + (size_t)p * np;
+        float *dst = out + (size_t)p * np;
+        for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+            const int j = j0 + r, i = i0 + threadIdx.x;
+            if (i < nx && j < ny) t[r][threadIdx.x] = src[(size_t)j * nx + i];
+        }
+        __syncthreads();
+        for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+            const int i = i0 + r, j = j0 + threadIdx.x;
+            if (i < nx && j < ny) dst[(size_t)i * ny + j] = t[threadIdx.x][r];
+        }
+        __syncthreads();
+    }
+}
+
 // J += the other groups' partials, in group order
 __global__ void face_sum_kernel(float *J, const float *Jp, int nparts, size_t n)
 {
@@ -305,7 +337,7 @@ static rt_status face_build(rt_grid *g)
                 const double ty = u[1] != 0.0 ? g->dy / std::fabs(u[1]) : INFINITY;
                 FaceDir d;
                 d.dir = q;
-                d.a_is_x = tx <= ty;
+                d.a_is_x = tx < ty;
                 const double ua = d.a_is_x ? u[0] : u[1], ub = d.a_is_x ? u[1] : u[0];
                 const double da = d.a_is_x ? g->dx : g->dy, db = d.a_is_x ? g->dy : g->dx;
                 const int na = d.a_is_x ? g->nx : g->ny;
@@ -343,6 +375,7 @@ static rt_status face_build(rt_grid *g)
     }
     first.push_back((int)dirs.size());
     FaceTables *t = new FaceTables;
+    for (const FaceDir &d : dirs) t->has_x |= d.a_is_x;
     t->ngroups = (int)first.size() - 1;
     t->wpb = wpb;
     t->nbpad = (std::max(g->nx, g->ny) + 31) / 32 * 32;
@@ -375,11 +408,14 @@ static rt_status face_build(rt_grid *g)
     return RT_OK;
 }
 
+// scratch: plane buffers [nlam][ndir][np], J partials [ngroups-1][nlam][npt], and, when some
+// direction's lines run along x, the transposed S and alpha [2][nlam][npt]
 static size_t face_scratch_bytes(const rt_grid *g, int nlam)
 {
     const size_t np = (size_t)g->nx * g->ny;
     return ((size_t)nlam * g->ndir * np +
-            (size_t)(g->face->ngroups - 1) * nlam * np * g->nz) * sizeof(float);
+            (size_t)(g->face->ngroups - 1 + 2 * g->face->has_x) * nlam * np * g->nz) *
+           sizeof(float);
 }
 
 rt_status face_prepare(rt_grid *g, int nlam)
@@ -402,6 +438,19 @@ rt_status face_formal_solution(rt_grid *g, int nlam, const float *alpha, const f
     a.J = J;
     a.buf = (float *)p;
     a.Jp = a.buf + (size_t)nlam * g->ndir * g->nx * g->ny;
+    a.ST = a.AT = nullptr;
+    if (t->has_x) {
+        float *ST = a.Jp + (size_t)(t->ngroups - 1) * nlam * g->npt;
+        float *AT = ST + (size_t)nlam * g->npt;
+        const int nplanes = nlam * g->nz;
+        const dim3 tg((g->nx + 31) / 32, (g->ny + 31) / 32, (unsigned)std::min(nplanes, 65535));
+        note_launch(2);
+        face_transpose_kernel<<<tg, dim3(32, 8), 0, st>>>(S, ST, g->nx, g->ny, nplanes);
+        face_transpose_kernel<<<tg, dim3(32, 8), 0, st>>>(alpha, AT, g->nx, g->ny, nplanes);
+        RT_CUDA(cudaGetLastError());
+        a.ST = ST;
+        a.AT = AT;
+    }
     a.dirs = t->d_dirs;
     a.steps = t->d_steps;
     a.first = t->d_first;
