@@ -314,6 +314,27 @@ rt_status rt_batch_formal_solution(rt_batch_t batch, const float *const *alpha,
                                    const float *const *S, int bc, float *const *J,
                                    void *stream);
 
+/* ---- site sampling (Sect. 2.4) -------------------------------------------------------------
+ * Rejection sampling of Voronoi sites: proposals uniform in the box are kept where the target f is
+ * at least a uniform rejection level times max f, until nsites are kept.  Proposal p = 0, 1, 2, ...
+ * is the Philox4x64-10 block (Salmon et al. 2011) of counter (p, 0, 0, 0) under key (seed, 0); its
+ * words w0..w3 give u_i = (w_i >> 11) 2^-53, the position (x0 + u0 (x1 - x0), y0 + u1 (y1 - y0),
+ * z0 + u2 (z1 - z0)) and the level u3.  f is trilinear between the mesh points
+ * (x0 + i (x1 - x0)/nx, y0 + j (y1 - y0)/ny, z[k]), periodic in x and y, clamped to
+ * [z[0], z[nz-1]] in z, each step lerp(a, b, t) = a + t (b - a) in IEEE double; the proposal is kept
+ * iff f(r) >= u3 max f.  The sites are the first nsites kept proposals in proposal order: the same
+ * for a seed on any device.  The Delaunay neighbours of the sites (rt_grid_desc) are built
+ * elsewhere.
+ * f: device float [nz][ny][nx], finite, >= 0, not all zero; z: host [nz] strictly ascending,
+ * nz >= 2; box: host [6] (x0, x1, y0, y1, z0, z1); xyz: device double [nsites][3], 8-byte aligned
+ * (output); *nproposals (host, may be NULL): the proposals drawn up to the last kept one.
+ * Allocates and frees a small device buffer; synchronises on stream once per 2^22 proposals.
+ * RT_EINVAL for a bad argument or target; RT_ENOCONV when 1000 nsites + 2^20 proposals have not
+ * given nsites sites. */
+rt_status rt_sample_sites(int nx, int ny, int nz, const double *z, const double *box,
+                          const float *f, int64_t nsites, uint64_t seed, double *xyz,
+                          int64_t *nproposals, void *stream);
+
 /* ---- allocation-free variant -------------------------------------------------------------- */
 /* No counterpart in the paper.  For callers that cannot allocate device memory (host callbacks
  * and stream-ordered code that must not synchronise the device, plugins whose host application

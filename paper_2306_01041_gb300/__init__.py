@@ -10,5 +10,6 @@ from .api import (IDW, Atmos, Atom, Batch, EmergentIntensity, Grid, RegularGrid,
                   VoronoiGrid, emergent_intensity, final_synthesis, formal_solution,
                   formal_solution_adjoint,
                   kernel_launches, lambda_iterate, lambda_iterate_ali, lambda_star,
-                  lte_populations, ng_extrapolate, source_terms, source_terms_adjoint, source_terms_lte,
+                  lte_populations, ng_extrapolate, sample_sites, source_terms,
+                  source_terms_adjoint, source_terms_lte,
                   source_terms_lte_adjoint, statistical_equilibrium, statistical_equilibrium_ali)

@@ -98,6 +98,8 @@ SIGNATURES = {
     "rt_batch_destroy": (None, [P]),
     "rt_batch_formal_solution": (c_int, [P, ctypes.POINTER(P), ctypes.POINTER(P), c_int,
                                          ctypes.POINTER(P), P]),
+    "rt_sample_sites": (c_int, [c_int, c_int, c_int, PD, PD, P, c_int64, ctypes.c_uint64, P,
+                                PI64, P]),
     "rt_last_error": (ctypes.c_char_p, []),
     "rt_kernel_launches": (ctypes.c_ulonglong, []),
 }

@@ -367,6 +367,26 @@ class IDW:
         return dst
 
 
+def sample_sites(f, z, box, nsites, seed, stream=None):
+    """Rejection sampling of nsites Voronoi sites (rt_sample_sites): f a float32 CUDA tensor
+    [nz][ny][nx] (the target at the mesh points), z the mesh heights, box (x0, x1, y0, y1, z0, z1).
+    Returns (xyz, nproposals): float64 CUDA [nsites][3] and the proposals drawn."""
+    fp = _dev(f, name="f")
+    if f.dim() != 3:
+        raise ValueError("f must be [nz][ny][nx]")
+    nz, ny, nx = f.shape
+    zz = _np(z, np.float64)
+    bx = _np(box, np.float64)
+    if len(zz) != nz or bx.shape != (6,):
+        raise ValueError("z must have nz entries and box six")
+    xyz = torch.empty((int(nsites), 3), dtype=torch.float64, device=f.device)
+    nprop = ctypes.c_int64()
+    check(lib().rt_sample_sites(nx, ny, nz, zz.ctypes.data_as(L.PD), bx.ctypes.data_as(L.PD),
+                                fp, int(nsites), int(seed), xyz.data_ptr(),
+                                ctypes.byref(nprop), _stream(stream)))
+    return xyz, nprop.value
+
+
 def final_synthesis(idw: IDW, mesh, atom: Atom, mesh_atm: Atmos, site_pops, stream=None):
     """Emergent vertical intensity [nlam][nx ny] of the mesh from converged site populations:
     interpolation to the mesh, opacities and source functions there, long characteristics
