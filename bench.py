@@ -551,6 +551,38 @@ def run_iterate(args):
                       "final_change": float(hist[-1])}))
 
 
+def run_sample(args):
+    """Rejection sampling of Voronoi sites on the GPU (rt_sample_sites) from the 500 nm continuum
+    opacity on the 128^3 mesh, floored at 1e-3 of its maximum."""
+    import torch
+    import paper_2306_01041_gb300 as rt
+    from synth import make_atmosphere
+    from synth.atmosphere import regular_fields
+    dev = torch.device("cuda", 0)
+    atm = make_atmosphere(0)
+    f, (x, y, z, dx, dy) = regular_fields(NX, NY, NZ, atm)
+    T = torch.tensor(f["T"], dtype=torch.float32, device=dev)
+    rho = torch.tensor(f["rho"], dtype=torch.float32, device=dev)
+    a, _ = rt.source_terms_lte(T, rho, atm.kappa0, 500e-9)
+    target = torch.clamp(a / a.max(), min=1e-3).reshape(NZ, NY, NX).contiguous()
+    box = (0.0, atm.Lx, 0.0, atm.Ly, atm.zmin, atm.zmax)
+    n = args.sample
+    for _ in range(2):
+        rt.sample_sites(target, z, box, n, 1)
+    torch.cuda.synchronize()
+    times = []
+    for s in range(max(1, args.steps)):
+        t0 = time.perf_counter()
+        _, nprop = rt.sample_sites(target, z, box, n, s + 2)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    ms = statistics.median(times) * 1e3
+    print(json.dumps({"workload": f"rejection sampling of {n} sites from the 500 nm continuum "
+                                  f"opacity on the {NX}x{NY}x{NZ} mesh", "ms": round(ms, 3),
+                      "proposals": nprop, "gproposals_s": round(nprop / ms / 1e6, 3),
+                      "msites_s": round(n / ms / 1e3, 3)}))
+
+
 def run_voronoi_batch(args):
     """The batched Voronoi formal solution alone on the first N atmospheres of the 8-atmosphere
     workload (52 wavelengths, 24 directions, populations at LTE): a smaller case of the batched
@@ -724,6 +756,8 @@ def main():
     ap.add_argument("--max-iter", type=int, default=300)
     ap.add_argument("--ng", type=int, default=0, help="Ng extrapolation period (0: off)")
     ap.add_argument("--tol", type=float, default=1e-3)
+    ap.add_argument("--sample", type=int, default=0,
+                    help="time only the rejection sampling of this many Voronoi sites")
     ap.add_argument("--scheme", choices=["plane", "face"], default="plane",
                     help="regular-grid short characteristics: plane to plane (default) or face "
                          "hitting")
@@ -742,6 +776,9 @@ def main():
         args.warmup = 3
     if args.voronoi_batch:
         run_voronoi_batch(args)
+        return
+    if args.sample:
+        run_sample(args)
         return
     if args.iterate:
         run_iterate(args)
