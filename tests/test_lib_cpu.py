@@ -129,3 +129,29 @@ def test_accelerated_and_synthesis_entry_points_reject_bad_arguments_on_host(lib
     assert lib.rt_idw_create(None, None, ctypes.byref(h)) == L.RT_EINVAL
     assert lib.rt_idw_interpolate(None, 3, None, None, None) == L.RT_EINVAL
     assert rt.kernel_launches() == n0
+
+
+def test_face_scheme_and_site_sampling_reject_bad_arguments_on_host(librt):
+    """rt_grid_set_scheme and rt_sample_sites validate on the host before any device work."""
+    import paper_2306_01041_gb300 as rt
+    from paper_2306_01041_gb300 import _lib as L
+    lib = rt.lib()
+    n0 = rt.kernel_launches()
+    assert lib.rt_grid_set_scheme(None, L.RT_SC_FACE) == L.RT_EINVAL
+    z = np.linspace(0.0, 1.0, 4)
+    box = np.array([0.0, 1.0, 0.0, 1.0, 0.0, 1.0])
+    fake = ctypes.c_void_p(256)                     # never dereferenced: rejected first
+    nprop = ctypes.c_int64()
+
+    def call(nx=2, ny=2, nz=4, zz=z, bx=box, n=10, xyz=fake):
+        return lib.rt_sample_sites(nx, ny, nz, zz.ctypes.data_as(L.PD), bx.ctypes.data_as(L.PD),
+                                   fake, n, 1, xyz, ctypes.byref(nprop), None)
+    assert call(nx=0) == L.RT_EINVAL
+    assert call(nz=1) == L.RT_EINVAL
+    assert call(n=0) == L.RT_EINVAL
+    assert call(zz=z[::-1].copy()) == L.RT_EINVAL
+    assert b"ascending" in lib.rt_last_error()
+    assert call(bx=np.array([0.0, 1.0, 0.0, 1.0, 1.0, 1.0])) == L.RT_EINVAL
+    assert call(xyz=ctypes.c_void_p(260)) == L.RT_EINVAL
+    assert b"aligned" in lib.rt_last_error()
+    assert rt.kernel_launches() == n0
