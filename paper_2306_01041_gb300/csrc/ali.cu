@@ -177,9 +177,11 @@ using namespace rt;
 extern "C" rt_status rt_lambda_star(rt_grid_t g, int nlam, const float *alpha, int bc, float *L,
                                     void *stream)
 {
-    if (!g || !alpha || !L) return fail(RT_EINVAL, "null argument");
-    if (nlam < 1) return fail(RT_EINVAL, "nlam must be >= 1");
-    if (bc != RT_BC_THERMAL && bc != RT_BC_ZERO && bc != RT_BC_ARRAY)
-        return fail(RT_EINVAL, "bc must be THERMAL, ZERO or ARRAY");
-    return lambda_star(g, nlam, alpha, bc, L, (cudaStream_t)stream);
+    return guarded([&]() -> rt_status {
+        if (!g || !alpha || !L) return fail(RT_EINVAL, "null argument");
+        if (nlam < 1) return fail(RT_EINVAL, "nlam must be >= 1");
+        if (bc != RT_BC_THERMAL && bc != RT_BC_ZERO && bc != RT_BC_ARRAY)
+            return fail(RT_EINVAL, "bc must be THERMAL, ZERO or ARRAY");
+        return lambda_star(g, nlam, alpha, bc, L, (cudaStream_t)stream);
+    });
 }

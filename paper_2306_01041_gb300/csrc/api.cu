@@ -445,90 +445,92 @@ unsigned long long rt_kernel_launches(void) { return g_launches.load(std::memory
 
 rt_status rt_grid_create(const rt_grid_desc *d, void *stream, rt_grid_t *out)
 {
-    if (!d || !out) return fail(RT_EINVAL, "null argument");
-    *out = nullptr;
-    if (d->ndir < 1 || d->ndir > MAX_DIR || !d->dirs || !d->wdir)
-        return fail(RT_EINVAL, "ndir must be 1..64 with dirs and wdir");
-    // host-side validation first, before any device call
-    if (d->kind == RT_GRID_REGULAR) {
-        if (d->nx < 1 || d->ny < 1 || d->nz < 2 || !(d->dx > 0) || !(d->dy > 0) || !d->z)
-            return fail(RT_EINVAL, "regular grid needs nx, ny >= 1, nz >= 2, dx, dy > 0 and z");
-        for (int k = 1; k < d->nz; ++k)
-            if (!(d->z[k] > d->z[k - 1])) return fail(RT_EINVAL, "z must be strictly ascending");
-    } else if (d->kind == RT_GRID_VORONOI) {
-        if (d->nsites < 1 || !d->xyz || !d->nbr_off || !d->nbr_idx)
-            return fail(RT_EINVAL, "Voronoi grid needs nsites >= 1, xyz, nbr_off and nbr_idx");
-        if (d->nsites > (int64_t)INT32_MAX / 2) return fail(RT_EINVAL, "too many sites");
-        if (!(d->box[1] > d->box[0] && d->box[3] > d->box[2] && d->box[5] > d->box[4]))
-            return fail(RT_EINVAL, "box must have positive extent");
-        if (d->nbr_off[0] != 0) return fail(RT_EINVAL, "nbr_off must start at 0");
-        for (int64_t i = 0; i < d->nsites; ++i)
-            if (d->nbr_off[i + 1] < d->nbr_off[i]) return fail(RT_EINVAL, "nbr_off not monotone");
-        for (int64_t e = 0; e < d->nbr_off[d->nsites]; ++e) {
-            const int64_t c = d->nbr_idx[e];
-            const int64_t k = c >= 0 ? c : ((-c - 1) >> 1);
-            if (k >= d->nsites) return fail(RT_EINVAL, "neighbour index out of range");
-            if (d->nbr_shift && (d->nbr_shift[e] < 0 || d->nbr_shift[e] > 8))
-                return fail(RT_EINVAL, "neighbour image shift out of range");
-        }
-        for (int64_t i = 0; i < d->nsites; ++i)
-            for (int c = 0; c < 3; ++c) {
-                const double v = d->xyz[3 * i + c];
-                if (!std::isfinite(v) || v < d->box[2 * c] || v > d->box[2 * c + 1])
-                    return fail(RT_EINVAL, "site outside the box");
+    return guarded([&]() -> rt_status {
+        if (!d || !out) return fail(RT_EINVAL, "null argument");
+        *out = nullptr;
+        if (d->ndir < 1 || d->ndir > MAX_DIR || !d->dirs || !d->wdir)
+            return fail(RT_EINVAL, "ndir must be 1..64 with dirs and wdir");
+        // host-side validation first, before any device call
+        if (d->kind == RT_GRID_REGULAR) {
+            if (d->nx < 1 || d->ny < 1 || d->nz < 2 || !(d->dx > 0) || !(d->dy > 0) || !d->z)
+                return fail(RT_EINVAL, "regular grid needs nx, ny >= 1, nz >= 2, dx, dy > 0 and z");
+            for (int k = 1; k < d->nz; ++k)
+                if (!(d->z[k] > d->z[k - 1])) return fail(RT_EINVAL, "z must be strictly ascending");
+        } else if (d->kind == RT_GRID_VORONOI) {
+            if (d->nsites < 1 || !d->xyz || !d->nbr_off || !d->nbr_idx)
+                return fail(RT_EINVAL, "Voronoi grid needs nsites >= 1, xyz, nbr_off and nbr_idx");
+            if (d->nsites > (int64_t)INT32_MAX / 2) return fail(RT_EINVAL, "too many sites");
+            if (!(d->box[1] > d->box[0] && d->box[3] > d->box[2] && d->box[5] > d->box[4]))
+                return fail(RT_EINVAL, "box must have positive extent");
+            if (d->nbr_off[0] != 0) return fail(RT_EINVAL, "nbr_off must start at 0");
+            for (int64_t i = 0; i < d->nsites; ++i)
+                if (d->nbr_off[i + 1] < d->nbr_off[i]) return fail(RT_EINVAL, "nbr_off not monotone");
+            for (int64_t e = 0; e < d->nbr_off[d->nsites]; ++e) {
+                const int64_t c = d->nbr_idx[e];
+                const int64_t k = c >= 0 ? c : ((-c - 1) >> 1);
+                if (k >= d->nsites) return fail(RT_EINVAL, "neighbour index out of range");
+                if (d->nbr_shift && (d->nbr_shift[e] < 0 || d->nbr_shift[e] > 8))
+                    return fail(RT_EINVAL, "neighbour image shift out of range");
             }
-    } else {
-        return fail(RT_EINVAL, "unknown grid kind");
-    }
-    for (int q = 0; q < d->ndir; ++q) {
-        const double *u = d->dirs + 3 * q;
-        const double nrm = std::sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-        if (!(std::fabs(nrm - 1.0) < 1e-6) || u[2] == 0.0 || !std::isfinite(d->wdir[q]))
-            return fail(RT_EINVAL, "directions must be unit vectors with mu_z != 0");
-    }
-    cudaStream_t st = (cudaStream_t)stream;
-    rt_grid *g = new (std::nothrow) rt_grid();
-    if (!g) return fail(RT_ENOMEM, "host allocation failed");
-    g->kind = d->kind;
-    g->ndir = d->ndir;
-    g->periodic = d->periodic_xy ? 1 : 0;
-    g->dirs.assign(d->dirs, d->dirs + 3 * d->ndir);
-    g->wdir.assign(d->wdir, d->wdir + d->ndir);
-    rt_status s = RT_OK;
-    for (int q = 0; q < g->ndir; ++q) {
-        const double *u = &g->dirs[3 * q];
-        double nrm = std::sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-        if (!(std::fabs(nrm - 1.0) < 1e-6) || u[2] == 0.0 || !std::isfinite(g->wdir[q])) {
-            delete g;
-            return fail(RT_EINVAL, "directions must be unit vectors with mu_z != 0");
+            for (int64_t i = 0; i < d->nsites; ++i)
+                for (int c = 0; c < 3; ++c) {
+                    const double v = d->xyz[3 * i + c];
+                    if (!std::isfinite(v) || v < d->box[2 * c] || v > d->box[2 * c + 1])
+                        return fail(RT_EINVAL, "site outside the box");
+                }
+        } else {
+            return fail(RT_EINVAL, "unknown grid kind");
         }
-        (u[2] > 0 ? g->dir_up : g->dir_dn).push_back(q);
-    }
-    cudaError_t e = cudaGetDevice(&g->device);
-    if (e == cudaSuccess) e = cudaMalloc(&g->d_err, sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMemsetAsync(g->d_err, 0, sizeof(unsigned), st);
-    if (e != cudaSuccess) {
-        delete g;
-        return cuda_fail(e, "grid device set-up");
-    }
-    double r_exp = d->r_exponent > 0 ? d->r_exponent : 7.0;
-    if (d->kind == RT_GRID_REGULAR) s = build_regular(g, d, st);
-    else if (d->kind == RT_GRID_VORONOI) s = build_voronoi(g, d, st, r_exp);
-    else s = fail(RT_EINVAL, "unknown grid kind");
-    if (s == RT_OK && !g->top.empty()) {
-        e = cudaMalloc(&g->d_top, g->top.size() * sizeof(int64_t));
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(g->d_top, g->top.data(), g->top.size() * sizeof(int64_t),
-                                cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) s = cuda_fail(e, "grid upload");
-    }
-    if (s != RT_OK) {
-        delete g;
-        return s;
-    }
-    *out = g;
-    return RT_OK;
+        for (int q = 0; q < d->ndir; ++q) {
+            const double *u = d->dirs + 3 * q;
+            const double nrm = std::sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+            if (!(std::fabs(nrm - 1.0) < 1e-6) || u[2] == 0.0 || !std::isfinite(d->wdir[q]))
+                return fail(RT_EINVAL, "directions must be unit vectors with mu_z != 0");
+        }
+        cudaStream_t st = (cudaStream_t)stream;
+        rt_grid *g = new (std::nothrow) rt_grid();
+        if (!g) return fail(RT_ENOMEM, "host allocation failed");
+        g->kind = d->kind;
+        g->ndir = d->ndir;
+        g->periodic = d->periodic_xy ? 1 : 0;
+        g->dirs.assign(d->dirs, d->dirs + 3 * d->ndir);
+        g->wdir.assign(d->wdir, d->wdir + d->ndir);
+        rt_status s = RT_OK;
+        for (int q = 0; q < g->ndir; ++q) {
+            const double *u = &g->dirs[3 * q];
+            double nrm = std::sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+            if (!(std::fabs(nrm - 1.0) < 1e-6) || u[2] == 0.0 || !std::isfinite(g->wdir[q])) {
+                delete g;
+                return fail(RT_EINVAL, "directions must be unit vectors with mu_z != 0");
+            }
+            (u[2] > 0 ? g->dir_up : g->dir_dn).push_back(q);
+        }
+        cudaError_t e = cudaGetDevice(&g->device);
+        if (e == cudaSuccess) e = cudaMalloc(&g->d_err, sizeof(unsigned));
+        if (e == cudaSuccess) e = cudaMemsetAsync(g->d_err, 0, sizeof(unsigned), st);
+        if (e != cudaSuccess) {
+            delete g;
+            return cuda_fail(e, "grid device set-up");
+        }
+        double r_exp = d->r_exponent > 0 ? d->r_exponent : 7.0;
+        if (d->kind == RT_GRID_REGULAR) s = build_regular(g, d, st);
+        else if (d->kind == RT_GRID_VORONOI) s = build_voronoi(g, d, st, r_exp);
+        else s = fail(RT_EINVAL, "unknown grid kind");
+        if (s == RT_OK && !g->top.empty()) {
+            e = cudaMalloc(&g->d_top, g->top.size() * sizeof(int64_t));
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(g->d_top, g->top.data(), g->top.size() * sizeof(int64_t),
+                                    cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) s = cuda_fail(e, "grid upload");
+        }
+        if (s != RT_OK) {
+            delete g;
+            return s;
+        }
+        *out = g;
+        return RT_OK;
+    });
 }
 
 void rt_grid_destroy(rt_grid_t g) { delete g; }
@@ -536,63 +538,73 @@ void rt_grid_destroy(rt_grid_t g) { delete g; }
 rt_status rt_grid_info(rt_grid_t g, int64_t *npt, int64_t *ntop, int *max_levels,
                        int64_t *n_fallback)
 {
-    if (!g) return fail(RT_EINVAL, "null grid");
-    if (npt) *npt = g->npt;
-    if (ntop) *ntop = (int64_t)g->top.size();
-    if (max_levels) *max_levels = g->max_levels;
-    if (n_fallback) *n_fallback = g->n_fallback;
-    return RT_OK;
+    return guarded([&]() -> rt_status {
+        if (!g) return fail(RT_EINVAL, "null grid");
+        if (npt) *npt = g->npt;
+        if (ntop) *ntop = (int64_t)g->top.size();
+        if (max_levels) *max_levels = g->max_levels;
+        if (n_fallback) *n_fallback = g->n_fallback;
+        return RT_OK;
+    });
 }
 
 rt_status rt_grid_tables(rt_grid_t g, int32_t *k, float *w, float *len, int32_t *level)
 {
-    if (!g || g->kind != RT_GRID_VORONOI) return fail(RT_EINVAL, "Voronoi grid required");
-    const size_t m = (size_t)g->ndir * g->nsites;
-    for (size_t i = 0; i < m; ++i) {
-        const Upwind &u = g->vt.h_up[i];
-        if (k) { k[2 * i] = u.k1; k[2 * i + 1] = u.k2; }
-        if (w) { w[2 * i] = u.w1; w[2 * i + 1] = 1.0f - u.w1; }
-        if (len) { len[2 * i] = u.l1; len[2 * i + 1] = u.l2; }
-        if (level) level[i] = g->vt.h_level[i];
-    }
-    return RT_OK;
+    return guarded([&]() -> rt_status {
+        if (!g || g->kind != RT_GRID_VORONOI) return fail(RT_EINVAL, "Voronoi grid required");
+        const size_t m = (size_t)g->ndir * g->nsites;
+        for (size_t i = 0; i < m; ++i) {
+            const Upwind &u = g->vt.h_up[i];
+            if (k) { k[2 * i] = u.k1; k[2 * i + 1] = u.k2; }
+            if (w) { w[2 * i] = u.w1; w[2 * i + 1] = 1.0f - u.w1; }
+            if (len) { len[2 * i] = u.l1; len[2 * i + 1] = u.l2; }
+            if (level) level[i] = g->vt.h_level[i];
+        }
+        return RT_OK;
+    });
 }
 
 rt_status rt_grid_top_points(rt_grid_t g, int64_t *idx)
 {
-    if (!g || !idx) return fail(RT_EINVAL, "null argument");
-    std::copy(g->top.begin(), g->top.end(), idx);
-    return RT_OK;
+    return guarded([&]() -> rt_status {
+        if (!g || !idx) return fail(RT_EINVAL, "null argument");
+        std::copy(g->top.begin(), g->top.end(), idx);
+        return RT_OK;
+    });
 }
 
 rt_status rt_formal_solution(rt_grid_t g, int nlam, const float *alpha, const float *S, int bc,
                              const float *I_bc, float *J, float *I_dir, void *stream)
 {
-    if (!g) return fail(RT_EINVAL, "null grid");
-    if (nlam < 1 || !alpha || !S || !J) return fail(RT_EINVAL, "nlam >= 1, alpha, S, J required");
-    if (bc < RT_BC_THERMAL || bc > RT_BC_ARRAY || (bc == RT_BC_ARRAY && !I_bc))
-        return fail(RT_EINVAL, "bad boundary condition");
-    if (!aligned16(alpha) || !aligned16(S) || !aligned16(J) || (I_dir && !aligned16(I_dir)) ||
-        (I_bc && !aligned16(I_bc)))
-        return fail(RT_EINVAL, "field pointers must be 16-byte aligned");
-    cudaStream_t st = (cudaStream_t)stream;
-    if (g->kind == RT_GRID_REGULAR)
-        return regular_formal_solution(g, nlam, alpha, S, bc, I_bc, J, I_dir, st);
-    return voronoi_formal_solution(g, nlam, alpha, S, bc, I_bc, J, I_dir, st);
+    return guarded([&]() -> rt_status {
+        if (!g) return fail(RT_EINVAL, "null grid");
+        if (nlam < 1 || !alpha || !S || !J) return fail(RT_EINVAL, "nlam >= 1, alpha, S, J required");
+        if (bc < RT_BC_THERMAL || bc > RT_BC_ARRAY || (bc == RT_BC_ARRAY && !I_bc))
+            return fail(RT_EINVAL, "bad boundary condition");
+        if (!aligned16(alpha) || !aligned16(S) || !aligned16(J) || (I_dir && !aligned16(I_dir)) ||
+            (I_bc && !aligned16(I_bc)))
+            return fail(RT_EINVAL, "field pointers must be 16-byte aligned");
+        cudaStream_t st = (cudaStream_t)stream;
+        if (g->kind == RT_GRID_REGULAR)
+            return regular_formal_solution(g, nlam, alpha, S, bc, I_bc, J, I_dir, st);
+        return voronoi_formal_solution(g, nlam, alpha, S, bc, I_bc, J, I_dir, st);
+    });
 }
 
 rt_status rt_emergent_intensity(rt_grid_t g, const double dir[3], int nlam, const float *alpha,
                                 const float *S, int bc, float *I_top, void *stream)
 {
-    if (!g || !dir || nlam < 1 || !alpha || !S || !I_top)
-        return fail(RT_EINVAL, "null argument");
-    if (!(dir[2] > 0)) return fail(RT_EINVAL, "the emergent direction needs mu_z > 0");
-    if (bc != RT_BC_THERMAL && bc != RT_BC_ZERO) return fail(RT_EINVAL, "bc must be THERMAL or ZERO");
-    if (!aligned16(alpha) || !aligned16(S) || !aligned16(I_top))
-        return fail(RT_EINVAL, "field pointers must be 16-byte aligned");
-    cudaStream_t st = (cudaStream_t)stream;
-    if (g->kind == RT_GRID_REGULAR) return regular_emergent(g, dir, nlam, alpha, S, bc, I_top, st);
-    return voronoi_emergent(g, dir, nlam, alpha, S, bc, I_top, st);
+    return guarded([&]() -> rt_status {
+        if (!g || !dir || nlam < 1 || !alpha || !S || !I_top)
+            return fail(RT_EINVAL, "null argument");
+        if (!(dir[2] > 0)) return fail(RT_EINVAL, "the emergent direction needs mu_z > 0");
+        if (bc != RT_BC_THERMAL && bc != RT_BC_ZERO) return fail(RT_EINVAL, "bc must be THERMAL or ZERO");
+        if (!aligned16(alpha) || !aligned16(S) || !aligned16(I_top))
+            return fail(RT_EINVAL, "field pointers must be 16-byte aligned");
+        cudaStream_t st = (cudaStream_t)stream;
+        if (g->kind == RT_GRID_REGULAR) return regular_emergent(g, dir, nlam, alpha, S, bc, I_top, st);
+        return voronoi_emergent(g, dir, nlam, alpha, S, bc, I_top, st);
+    });
 }
 
 size_t rt_adjoint_workspace_size(rt_grid_t g, int nlam, int stride)
@@ -607,22 +619,24 @@ rt_status rt_formal_solution_adjoint(rt_grid_t g, const double dir[3], int nlam,
                                      const float *gI_top, float *g_alpha, float *g_S,
                                      int stride, void *ws, size_t ws_bytes, void *stream)
 {
-    if (!g || !dir || nlam < 1 || !alpha || !S || !gI_top || !g_alpha || !g_S)
-        return fail(RT_EINVAL, "null argument");
-    if (!(dir[2] > 0)) return fail(RT_EINVAL, "the emergent direction needs mu_z > 0");
-    if (bc != RT_BC_THERMAL && bc != RT_BC_ZERO) return fail(RT_EINVAL, "bc must be THERMAL or ZERO");
-    if (stride < 1) return fail(RT_EINVAL, "ckpt_stride must be >= 1");
-    if (!aligned16(alpha) || !aligned16(S) || !aligned16(gI_top) || !aligned16(g_alpha) ||
-        !aligned16(g_S) || (ws && !aligned16(ws)))
-        return fail(RT_EINVAL, "pointers must be 16-byte aligned");
-    size_t need = rt_adjoint_workspace_size(g, nlam, stride);
-    if (!ws || ws_bytes < need) return fail(RT_EINVAL, "workspace too small");
-    cudaStream_t st = (cudaStream_t)stream;
-    if (g->kind == RT_GRID_REGULAR)
-        return regular_adjoint(g, dir, nlam, alpha, S, bc, gI_top, g_alpha, g_S, stride, ws,
-                               ws_bytes, st);
-    return voronoi_adjoint(g, dir, nlam, alpha, S, bc, gI_top, g_alpha, g_S, stride, ws, ws_bytes,
-                           st);
+    return guarded([&]() -> rt_status {
+        if (!g || !dir || nlam < 1 || !alpha || !S || !gI_top || !g_alpha || !g_S)
+            return fail(RT_EINVAL, "null argument");
+        if (!(dir[2] > 0)) return fail(RT_EINVAL, "the emergent direction needs mu_z > 0");
+        if (bc != RT_BC_THERMAL && bc != RT_BC_ZERO) return fail(RT_EINVAL, "bc must be THERMAL or ZERO");
+        if (stride < 1) return fail(RT_EINVAL, "ckpt_stride must be >= 1");
+        if (!aligned16(alpha) || !aligned16(S) || !aligned16(gI_top) || !aligned16(g_alpha) ||
+            !aligned16(g_S) || (ws && !aligned16(ws)))
+            return fail(RT_EINVAL, "pointers must be 16-byte aligned");
+        size_t need = rt_adjoint_workspace_size(g, nlam, stride);
+        if (!ws || ws_bytes < need) return fail(RT_EINVAL, "workspace too small");
+        cudaStream_t st = (cudaStream_t)stream;
+        if (g->kind == RT_GRID_REGULAR)
+            return regular_adjoint(g, dir, nlam, alpha, S, bc, gI_top, g_alpha, g_S, stride, ws,
+                                   ws_bytes, st);
+        return voronoi_adjoint(g, dir, nlam, alpha, S, bc, gI_top, g_alpha, g_S, stride, ws, ws_bytes,
+                               st);
+    });
 }
 
 }  // extern "C"

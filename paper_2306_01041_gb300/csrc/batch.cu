@@ -264,131 +264,133 @@ extern "C" {
 rt_status rt_batch_create(const rt_grid_t *grids, int ngrids, int nlam, const int *lam_chunk,
                           int threads, rt_batch_t *out)
 {
-    if (!grids || ngrids < 1 || nlam < 1 || !out) return fail(RT_EINVAL, "bad argument");
-    *out = nullptr;
-    rt_batch *b = new (std::nothrow) rt_batch();
-    if (!b) return fail(RT_ENOMEM, "host allocation failed");
-    b->nlam = nlam;
-    b->ndir = grids[0]->ndir;
-    b->threads = threads > 0 ? threads : 512;
-    if (b->threads > 512 || b->threads % 32) {
-        delete b;
-        return fail(RT_EINVAL, "threads must be a multiple of 32 up to 512");
-    }
-    int64_t ntot = 0, nmin = INT64_MAX;
-    for (int i = 0; i < ngrids; ++i) {
-        rt_grid *g = grids[i];
-        if (!g || g->kind != RT_GRID_VORONOI || g->ndir != b->ndir) {
+    return guarded([&]() -> rt_status {
+        if (!grids || ngrids < 1 || nlam < 1 || !out) return fail(RT_EINVAL, "bad argument");
+        *out = nullptr;
+        rt_batch *b = new (std::nothrow) rt_batch();
+        if (!b) return fail(RT_ENOMEM, "host allocation failed");
+        b->nlam = nlam;
+        b->ndir = grids[0]->ndir;
+        b->threads = threads > 0 ? threads : 512;
+        if (b->threads > 512 || b->threads % 32) {
             delete b;
-            return fail(RT_EINVAL, "batch grids must be Voronoi grids with the same directions");
+            return fail(RT_EINVAL, "threads must be a multiple of 32 up to 512");
         }
-        for (int d = 0; d < g->ndir; ++d)
-            if (g->wdir[d] != grids[0]->wdir[d] || g->dirs[3 * d + 2] != grids[0]->dirs[3 * d + 2]) {
+        int64_t ntot = 0, nmin = INT64_MAX;
+        for (int i = 0; i < ngrids; ++i) {
+            rt_grid *g = grids[i];
+            if (!g || g->kind != RT_GRID_VORONOI || g->ndir != b->ndir) {
                 delete b;
-                return fail(RT_EINVAL, "batch grids must share the quadrature");
+                return fail(RT_EINVAL, "batch grids must be Voronoi grids with the same directions");
             }
-        b->grids.push_back(g);
-        ntot += g->nsites;
-        nmin = std::min<int64_t>(nmin, g->nsites);
-    }
-    int dev = 0, nsm = 0, per_sm = 0;
-    RT_CUDA(cudaGetDevice(&dev));
-    RT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    RT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_sweep_kernel, b->threads, 0));
-    if (per_sm < 1) {
-        delete b;
-        return fail(RT_ECAPACITY, "the batched sweep kernel cannot be resident");
-    }
-    b->blocks = nsm * per_sm;
-    // items: default chunk sizes make every item carry about the same number of (site, lambda,
-    // direction) updates, about total / (2 * resident blocks)
-    for (int i = 0; i < ngrids; ++i) {
-        int lc;
-        if (lam_chunk) {
-            lc = lam_chunk[i];
-        } else {
-            const double target = (double)ntot * nlam * b->ndir / (2.0 * b->blocks);
-            lc = (int)std::lround(target / (double)grids[i]->nsites);
+            for (int d = 0; d < g->ndir; ++d)
+                if (g->wdir[d] != grids[0]->wdir[d] || g->dirs[3 * d + 2] != grids[0]->dirs[3 * d + 2]) {
+                    delete b;
+                    return fail(RT_EINVAL, "batch grids must share the quadrature");
+                }
+            b->grids.push_back(g);
+            ntot += g->nsites;
+            nmin = std::min<int64_t>(nmin, g->nsites);
         }
-        lc = std::max(1, std::min(nlam, lc));
-        for (int d = 0; d < b->ndir; ++d)
-            for (int c0 = 0; c0 < nlam; c0 += lc)
-                b->h_items.push_back(BatchItem{i, d, c0, std::min(lc, nlam - c0)});
-    }
-    std::stable_sort(b->h_items.begin(), b->h_items.end(), [&](const BatchItem &x, const BatchItem &y) {
-        return (double)grids[x.grid]->nsites * x.lc > (double)grids[y.grid]->nsites * y.lc;
-    });
-    // device tables
-    std::vector<int64_t> lvl;
-    std::vector<int32_t> base;
-    std::vector<size_t> base_at(ngrids);
-    for (int i = 0; i < ngrids; ++i) {
-        base_at[i] = base.size();
-        for (int d = 0; d < b->ndir; ++d) {
+        int dev = 0, nsm = 0, per_sm = 0;
+        RT_CUDA(cudaGetDevice(&dev));
+        RT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        RT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_sweep_kernel, b->threads, 0));
+        if (per_sm < 1) {
+            delete b;
+            return fail(RT_ECAPACITY, "the batched sweep kernel cannot be resident");
+        }
+        b->blocks = nsm * per_sm;
+        // items: default chunk sizes make every item carry about the same number of (site, lambda,
+        // direction) updates, about total / (2 * resident blocks)
+        for (int i = 0; i < ngrids; ++i) {
+            int lc;
+            if (lam_chunk) {
+                lc = lam_chunk[i];
+            } else {
+                const double target = (double)ntot * nlam * b->ndir / (2.0 * b->blocks);
+                lc = (int)std::lround(target / (double)grids[i]->nsites);
+            }
+            lc = std::max(1, std::min(nlam, lc));
+            for (int d = 0; d < b->ndir; ++d)
+                for (int c0 = 0; c0 < nlam; c0 += lc)
+                    b->h_items.push_back(BatchItem{i, d, c0, std::min(lc, nlam - c0)});
+        }
+        std::stable_sort(b->h_items.begin(), b->h_items.end(), [&](const BatchItem &x, const BatchItem &y) {
+            return (double)grids[x.grid]->nsites * x.lc > (double)grids[y.grid]->nsites * y.lc;
+        });
+        // device tables
+        std::vector<int64_t> lvl;
+        std::vector<int32_t> base;
+        std::vector<size_t> base_at(ngrids);
+        for (int i = 0; i < ngrids; ++i) {
+            base_at[i] = base.size();
+            for (int d = 0; d < b->ndir; ++d) {
+                base.push_back((int32_t)lvl.size());
+                const auto &o = grids[i]->vt.lvl_off[d];
+                lvl.insert(lvl.end(), o.begin(), o.end());
+            }
             base.push_back((int32_t)lvl.size());
-            const auto &o = grids[i]->vt.lvl_off[d];
-            lvl.insert(lvl.end(), o.begin(), o.end());
         }
-        base.push_back((int32_t)lvl.size());
-    }
-    size_t fsz = 0;
-    for (int i = 0; i < ngrids; ++i) fsz += batch_grid_floats(grids[i]->nsites, nlam, b->ndir);
-    std::vector<float> wd(b->ndir), uf(b->ndir);
-    for (int d = 0; d < b->ndir; ++d) {
-        wd[d] = (float)grids[0]->wdir[d];
-        uf[d] = grids[0]->dirs[3 * d + 2] > 0 ? 1.f : 0.f;
-    }
-    cudaError_t e = cudaSuccess;
-#define BT(x)                                                   \
-    do {                                                        \
-        if (e == cudaSuccess) e = (x);                          \
-    } while (0)
-    BT(cudaMalloc(&b->d_items, b->h_items.size() * sizeof(BatchItem)));
-    BT(cudaMalloc(&b->d_grids, ngrids * sizeof(BatchGridDev)));
-    BT(cudaMalloc(&b->d_lvl, lvl.size() * sizeof(int64_t)));
-    BT(cudaMalloc(&b->d_lvl_base, base.size() * sizeof(int32_t)));
-    BT(cudaMalloc(&b->d_wdir, b->ndir * sizeof(float)));
-    BT(cudaMalloc(&b->d_upf, b->ndir * sizeof(float)));
-    BT(cudaMalloc(&b->d_fields, fsz * sizeof(float)));
-    BT(cudaMalloc(&b->d_queue, sizeof(int)));
-    BT(cudaMalloc(&b->d_err, sizeof(unsigned)));
-    if (e != cudaSuccess) {
-        delete b;
-        return cuda_fail(e, "batch allocation");
-    }
-    float *f = b->d_fields;
-    for (int i = 0; i < ngrids; ++i) {
-        rt_grid *g = grids[i];
-        const size_t m = (size_t)g->nsites * nlam;
-        BatchGridDev gd;
-        gd.up = g->vt.d_up;
-        gd.order = g->vt.d_order;
-        gd.lvl = b->d_lvl;
-        gd.lvl_base = b->d_lvl_base + base_at[i];
-        gd.SA = reinterpret_cast<const float2 *>(f);
-        gd.J = f + 2 * m;
-        gd.I = f + 3 * m;
-        gd.n = (int)g->nsites;
-        f += batch_grid_floats(g->nsites, nlam, b->ndir);
-        b->h_grids.push_back(gd);
-    }
-    BT(cudaMemcpy(b->d_items, b->h_items.data(), b->h_items.size() * sizeof(BatchItem),
-                  cudaMemcpyHostToDevice));
-    BT(cudaMemcpy(b->d_grids, b->h_grids.data(), ngrids * sizeof(BatchGridDev),
-                  cudaMemcpyHostToDevice));
-    BT(cudaMemcpy(b->d_lvl, lvl.data(), lvl.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
-    BT(cudaMemcpy(b->d_lvl_base, base.data(), base.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-    BT(cudaMemcpy(b->d_wdir, wd.data(), b->ndir * sizeof(float), cudaMemcpyHostToDevice));
-    BT(cudaMemcpy(b->d_upf, uf.data(), b->ndir * sizeof(float), cudaMemcpyHostToDevice));
-    BT(cudaMemset(b->d_err, 0, sizeof(unsigned)));
-    b->err = ngrids == 1 ? grids[0]->d_err : b->d_err;
-#undef BT
-    if (e != cudaSuccess) {
-        delete b;
-        return cuda_fail(e, "batch upload");
-    }
-    *out = b;
-    return RT_OK;
+        size_t fsz = 0;
+        for (int i = 0; i < ngrids; ++i) fsz += batch_grid_floats(grids[i]->nsites, nlam, b->ndir);
+        std::vector<float> wd(b->ndir), uf(b->ndir);
+        for (int d = 0; d < b->ndir; ++d) {
+            wd[d] = (float)grids[0]->wdir[d];
+            uf[d] = grids[0]->dirs[3 * d + 2] > 0 ? 1.f : 0.f;
+        }
+        cudaError_t e = cudaSuccess;
+    #define BT(x)                                                   \
+        do {                                                        \
+            if (e == cudaSuccess) e = (x);                          \
+        } while (0)
+        BT(cudaMalloc(&b->d_items, b->h_items.size() * sizeof(BatchItem)));
+        BT(cudaMalloc(&b->d_grids, ngrids * sizeof(BatchGridDev)));
+        BT(cudaMalloc(&b->d_lvl, lvl.size() * sizeof(int64_t)));
+        BT(cudaMalloc(&b->d_lvl_base, base.size() * sizeof(int32_t)));
+        BT(cudaMalloc(&b->d_wdir, b->ndir * sizeof(float)));
+        BT(cudaMalloc(&b->d_upf, b->ndir * sizeof(float)));
+        BT(cudaMalloc(&b->d_fields, fsz * sizeof(float)));
+        BT(cudaMalloc(&b->d_queue, sizeof(int)));
+        BT(cudaMalloc(&b->d_err, sizeof(unsigned)));
+        if (e != cudaSuccess) {
+            delete b;
+            return cuda_fail(e, "batch allocation");
+        }
+        float *f = b->d_fields;
+        for (int i = 0; i < ngrids; ++i) {
+            rt_grid *g = grids[i];
+            const size_t m = (size_t)g->nsites * nlam;
+            BatchGridDev gd;
+            gd.up = g->vt.d_up;
+            gd.order = g->vt.d_order;
+            gd.lvl = b->d_lvl;
+            gd.lvl_base = b->d_lvl_base + base_at[i];
+            gd.SA = reinterpret_cast<const float2 *>(f);
+            gd.J = f + 2 * m;
+            gd.I = f + 3 * m;
+            gd.n = (int)g->nsites;
+            f += batch_grid_floats(g->nsites, nlam, b->ndir);
+            b->h_grids.push_back(gd);
+        }
+        BT(cudaMemcpy(b->d_items, b->h_items.data(), b->h_items.size() * sizeof(BatchItem),
+                      cudaMemcpyHostToDevice));
+        BT(cudaMemcpy(b->d_grids, b->h_grids.data(), ngrids * sizeof(BatchGridDev),
+                      cudaMemcpyHostToDevice));
+        BT(cudaMemcpy(b->d_lvl, lvl.data(), lvl.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+        BT(cudaMemcpy(b->d_lvl_base, base.data(), base.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        BT(cudaMemcpy(b->d_wdir, wd.data(), b->ndir * sizeof(float), cudaMemcpyHostToDevice));
+        BT(cudaMemcpy(b->d_upf, uf.data(), b->ndir * sizeof(float), cudaMemcpyHostToDevice));
+        BT(cudaMemset(b->d_err, 0, sizeof(unsigned)));
+        b->err = ngrids == 1 ? grids[0]->d_err : b->d_err;
+    #undef BT
+        if (e != cudaSuccess) {
+            delete b;
+            return cuda_fail(e, "batch upload");
+        }
+        *out = b;
+        return RT_OK;
+    });
 }
 
 void rt_batch_destroy(rt_batch_t b) { delete b; }
@@ -396,40 +398,42 @@ void rt_batch_destroy(rt_batch_t b) { delete b; }
 rt_status rt_batch_formal_solution(rt_batch_t b, const float *const *alpha, const float *const *S,
                                    int bc, float *const *J, void *stream)
 {
-    if (!b || !alpha || !S || !J) return fail(RT_EINVAL, "null argument");
-    if (bc != RT_BC_THERMAL && bc != RT_BC_ZERO) return fail(RT_EINVAL, "bc must be THERMAL or ZERO");
-    cudaStream_t st = (cudaStream_t)stream;
-    const int ng = (int)b->grids.size();
-    for (int i = 0; i < ng; ++i) {
-        if (!alpha[i] || !S[i] || !J[i]) return fail(RT_EINVAL, "null field");
-        const BatchGridDev &g = b->h_grids[i];
-        transpose_pair(S[i], alpha[i], const_cast<float2 *>(g.SA), b->nlam, g.n, st);
-    }
-    RT_CUDA(cudaMemsetAsync(b->d_queue, 0, sizeof(int), st));
-    BatchArgs a;
-    a.grids = b->d_grids;
-    a.items = b->d_items;
-    a.queue = b->d_queue;
-    a.wdir = b->d_wdir;
-    a.up_flag = b->d_upf;
-    a.err = b->err;
-    a.nitems = (int)b->h_items.size();
-    a.ndir = b->ndir;
-    a.nlam = b->nlam;
-    a.bc = bc;
-    const int blocks = std::min<int>(b->blocks, a.nitems);
-    note_launch();
-    batch_sweep_kernel<<<blocks, b->threads, 0, st>>>(a);
-    for (int i = 0; i < ng; ++i) {
-        const BatchGridDev &g = b->h_grids[i];
-        const size_t m = (size_t)g.n * b->nlam;
+    return guarded([&]() -> rt_status {
+        if (!b || !alpha || !S || !J) return fail(RT_EINVAL, "null argument");
+        if (bc != RT_BC_THERMAL && bc != RT_BC_ZERO) return fail(RT_EINVAL, "bc must be THERMAL or ZERO");
+        cudaStream_t st = (cudaStream_t)stream;
+        const int ng = (int)b->grids.size();
+        for (int i = 0; i < ng; ++i) {
+            if (!alpha[i] || !S[i] || !J[i]) return fail(RT_EINVAL, "null field");
+            const BatchGridDev &g = b->h_grids[i];
+            transpose_pair(S[i], alpha[i], const_cast<float2 *>(g.SA), b->nlam, g.n, st);
+        }
+        RT_CUDA(cudaMemsetAsync(b->d_queue, 0, sizeof(int), st));
+        BatchArgs a;
+        a.grids = b->d_grids;
+        a.items = b->d_items;
+        a.queue = b->d_queue;
+        a.wdir = b->d_wdir;
+        a.up_flag = b->d_upf;
+        a.err = b->err;
+        a.nitems = (int)b->h_items.size();
+        a.ndir = b->ndir;
+        a.nlam = b->nlam;
+        a.bc = bc;
+        const int blocks = std::min<int>(b->blocks, a.nitems);
         note_launch();
-        batch_reduce_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(g.I, g.J, b->d_wdir,
-                                                                         b->ndir, m, b->err);
-        transpose_b(g.J, J[i], g.n, b->nlam, st);
-    }
-    RT_CUDA(cudaGetLastError());
-    return RT_OK;
+        batch_sweep_kernel<<<blocks, b->threads, 0, st>>>(a);
+        for (int i = 0; i < ng; ++i) {
+            const BatchGridDev &g = b->h_grids[i];
+            const size_t m = (size_t)g.n * b->nlam;
+            note_launch();
+            batch_reduce_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(g.I, g.J, b->d_wdir,
+                                                                             b->ndir, m, b->err);
+            transpose_b(g.J, J[i], g.n, b->nlam, st);
+        }
+        RT_CUDA(cudaGetLastError());
+        return RT_OK;
+    });
 }
 
 }  // extern "C"

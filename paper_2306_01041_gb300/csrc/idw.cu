@@ -149,73 +149,79 @@ extern "C" {
 
 rt_status rt_idw_create(rt_grid_t voronoi, rt_grid_t mesh, rt_idw_t *out)
 {
-    if (!voronoi || !mesh || !out) return fail(RT_EINVAL, "null argument");
-    *out = nullptr;
-    if (voronoi->kind != RT_GRID_VORONOI || mesh->kind != RT_GRID_REGULAR)
-        return fail(RT_EINVAL, "rt_idw_create takes a Voronoi grid and a regular grid");
-    if (voronoi->nsites < 2) return fail(RT_EINVAL, "need at least two sites");
-    rt_idw *t = new (std::nothrow) rt_idw();
-    if (!t) return fail(RT_ENOMEM, "host allocation failed");
-    t->npt = mesh->npt;
-    t->nsites = voronoi->nsites;
-    const Bins b = make_bins(voronoi);
-    t->h_k.resize(t->npt);
-    t->h_w.resize(t->npt);
-    const int nx = mesh->nx, ny = mesh->ny;
-#pragma omp parallel for schedule(dynamic, 256)
-    for (int64_t p = 0; p < t->npt; ++p) {
-        const int i = (int)(p % nx), j = (int)((p / nx) % ny), k = (int)(p / ((int64_t)nx * ny));
-        const double q[3] = {i * mesh->dx, j * mesh->dy, mesh->z[k]};
-        Near n1, n2;
-        two_nearest(voronoi, b, q, n1, n2);
-        const double d1 = std::sqrt(n1.d2), d2 = std::sqrt(n2.d2);
-        float w1 = 1.f, w2 = 0.f;
-        if (d1 > 0.0) {
-            const double a = 1.0 / d1, c = 1.0 / d2;
-            w1 = (float)(a / (a + c));
-            w2 = (float)(c / (a + c));
+    return guarded([&]() -> rt_status {
+        if (!voronoi || !mesh || !out) return fail(RT_EINVAL, "null argument");
+        *out = nullptr;
+        if (voronoi->kind != RT_GRID_VORONOI || mesh->kind != RT_GRID_REGULAR)
+            return fail(RT_EINVAL, "rt_idw_create takes a Voronoi grid and a regular grid");
+        if (voronoi->nsites < 2) return fail(RT_EINVAL, "need at least two sites");
+        rt_idw *t = new (std::nothrow) rt_idw();
+        if (!t) return fail(RT_ENOMEM, "host allocation failed");
+        t->npt = mesh->npt;
+        t->nsites = voronoi->nsites;
+        const Bins b = make_bins(voronoi);
+        t->h_k.resize(t->npt);
+        t->h_w.resize(t->npt);
+        const int nx = mesh->nx, ny = mesh->ny;
+    #pragma omp parallel for schedule(dynamic, 256)
+        for (int64_t p = 0; p < t->npt; ++p) {
+            const int i = (int)(p % nx), j = (int)((p / nx) % ny), k = (int)(p / ((int64_t)nx * ny));
+            const double q[3] = {i * mesh->dx, j * mesh->dy, mesh->z[k]};
+            Near n1, n2;
+            two_nearest(voronoi, b, q, n1, n2);
+            const double d1 = std::sqrt(n1.d2), d2 = std::sqrt(n2.d2);
+            float w1 = 1.f, w2 = 0.f;
+            if (d1 > 0.0) {
+                const double a = 1.0 / d1, c = 1.0 / d2;
+                w1 = (float)(a / (a + c));
+                w2 = (float)(c / (a + c));
+            }
+            t->h_k[p] = make_int2(n1.k, n2.k);
+            t->h_w[p] = make_float2(w1, w2);
         }
-        t->h_k[p] = make_int2(n1.k, n2.k);
-        t->h_w[p] = make_float2(w1, w2);
-    }
-    cudaError_t e = cudaMalloc(&t->d_k, t->npt * sizeof(int2));
-    if (e == cudaSuccess) e = cudaMalloc(&t->d_w, t->npt * sizeof(float2));
-    if (e == cudaSuccess)
-        e = cudaMemcpy(t->d_k, t->h_k.data(), t->npt * sizeof(int2), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(t->d_w, t->h_w.data(), t->npt * sizeof(float2), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) {
-        delete t;
-        return cuda_fail(e, "idw table upload");
-    }
-    *out = t;
-    return RT_OK;
+        cudaError_t e = cudaMalloc(&t->d_k, t->npt * sizeof(int2));
+        if (e == cudaSuccess) e = cudaMalloc(&t->d_w, t->npt * sizeof(float2));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(t->d_k, t->h_k.data(), t->npt * sizeof(int2), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(t->d_w, t->h_w.data(), t->npt * sizeof(float2), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            delete t;
+            return cuda_fail(e, "idw table upload");
+        }
+        *out = t;
+        return RT_OK;
+    });
 }
 
 void rt_idw_destroy(rt_idw_t t) { delete t; }
 
 rt_status rt_idw_table(rt_idw_t t, int32_t *k, float *w)
 {
-    if (!t || !k || !w) return fail(RT_EINVAL, "null argument");
-    for (int64_t p = 0; p < t->npt; ++p) {
-        k[2 * p] = t->h_k[p].x;
-        k[2 * p + 1] = t->h_k[p].y;
-        w[2 * p] = t->h_w[p].x;
-        w[2 * p + 1] = t->h_w[p].y;
-    }
-    return RT_OK;
+    return guarded([&]() -> rt_status {
+        if (!t || !k || !w) return fail(RT_EINVAL, "null argument");
+        for (int64_t p = 0; p < t->npt; ++p) {
+            k[2 * p] = t->h_k[p].x;
+            k[2 * p + 1] = t->h_k[p].y;
+            w[2 * p] = t->h_w[p].x;
+            w[2 * p + 1] = t->h_w[p].y;
+        }
+        return RT_OK;
+    });
 }
 
 rt_status rt_idw_interpolate(rt_idw_t t, int nf, const float *src, float *dst, void *stream)
 {
-    if (!t || !src || !dst) return fail(RT_EINVAL, "null argument");
-    if (nf < 1) return fail(RT_EINVAL, "nf must be >= 1");
-    const int64_t work = t->npt * nf;
-    note_launch();
-    idw_gather_kernel<<<(unsigned)((work + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
-        t->d_k, t->d_w, src, dst, t->npt, t->nsites, nf);
-    RT_CUDA(cudaGetLastError());
-    return RT_OK;
+    return guarded([&]() -> rt_status {
+        if (!t || !src || !dst) return fail(RT_EINVAL, "null argument");
+        if (nf < 1) return fail(RT_EINVAL, "nf must be >= 1");
+        const int64_t work = t->npt * nf;
+        note_launch();
+        idw_gather_kernel<<<(unsigned)((work + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+            t->d_k, t->d_w, src, dst, t->npt, t->nsites, nf);
+        RT_CUDA(cudaGetLastError());
+        return RT_OK;
+    });
 }
 
 }  // extern "C"

@@ -93,7 +93,9 @@ extern "C" rt_status rt_ng_extrapolate(int64_t n, const float *x0, const float *
                                        const float *x2, const float *x3, float *out,
                                        void *scratch, int *ok, void *stream)
 {
-    if (n < 1 || !x0 || !x1 || !x2 || !x3 || !out || !scratch || !ok)
-        return fail(RT_EINVAL, "bad argument");
-    return ng_extrapolate(x0, x1, x2, x3, n, out, scratch, (cudaStream_t)stream, ok);
+    return guarded([&]() -> rt_status {
+        if (n < 1 || !x0 || !x1 || !x2 || !x3 || !out || !scratch || !ok)
+            return fail(RT_EINVAL, "bad argument");
+        return ng_extrapolate(x0, x1, x2, x3, n, out, scratch, (cudaStream_t)stream, ok);
+    });
 }

@@ -762,101 +762,115 @@ extern "C" {
 rt_status rt_source_terms_lte(int64_t npt, const float *T, const float *rho, double kappa0,
                               double lam, float *alpha, float *S, void *stream)
 {
-    if (npt < 1 || !T || !rho || !alpha || !S || !(lam > 0)) return fail(RT_EINVAL, "bad argument");
-    const double hc = kH * kC;
-    note_launch();
-    lte_source_kernel<<<(unsigned)((npt + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
-        npt, T, rho, (float)kappa0, (float)(2.0 * hc * kC / std::pow(lam, 5)),
-        (float)(hc / (lam * kK)), alpha, S);
-    RT_CUDA(cudaGetLastError());
-    return RT_OK;
+    return guarded([&]() -> rt_status {
+        if (npt < 1 || !T || !rho || !alpha || !S || !(lam > 0)) return fail(RT_EINVAL, "bad argument");
+        const double hc = kH * kC;
+        note_launch();
+        lte_source_kernel<<<(unsigned)((npt + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+            npt, T, rho, (float)kappa0, (float)(2.0 * hc * kC / std::pow(lam, 5)),
+            (float)(hc / (lam * kK)), alpha, S);
+        RT_CUDA(cudaGetLastError());
+        return RT_OK;
+    });
 }
 
 rt_status rt_source_terms_lte_adjoint(int64_t npt, const float *T, const float *rho,
                                       double kappa0, double lam, const float *g_alpha,
                                       const float *g_S, float *g_T, void *stream)
 {
-    if (npt < 1 || !T || !rho || !g_alpha || !g_S || !g_T) return fail(RT_EINVAL, "bad argument");
-    const double hc = kH * kC;
-    note_launch();
-    lte_source_adjoint_kernel<<<(unsigned)((npt + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
-        npt, T, rho, (float)kappa0, (float)(2.0 * hc * kC / std::pow(lam, 5)),
-        (float)(hc / (lam * kK)), g_alpha, g_S, g_T);
-    RT_CUDA(cudaGetLastError());
-    return RT_OK;
+    return guarded([&]() -> rt_status {
+        if (npt < 1 || !T || !rho || !g_alpha || !g_S || !g_T) return fail(RT_EINVAL, "bad argument");
+        const double hc = kH * kC;
+        note_launch();
+        lte_source_adjoint_kernel<<<(unsigned)((npt + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+            npt, T, rho, (float)kappa0, (float)(2.0 * hc * kC / std::pow(lam, 5)),
+            (float)(hc / (lam * kK)), g_alpha, g_S, g_T);
+        RT_CUDA(cudaGetLastError());
+        return RT_OK;
+    });
 }
 
 rt_status rt_source_terms(rt_grid_t g, const rt_atom *atom, const rt_atmos *atm,
                           const float *pops, float *alpha, float *S, void *stream)
 {
-    RT_TRY(check_atmos(g, atm, pops));
-    if (!alpha || !S) return fail(RT_EINVAL, "null output");
-    RT_TRY(load_atom(atom));
-    const int64_t n = g->npt;
-    note_launch();
-    source_terms_kernel<<<(unsigned)((n + 127) / 128), 128, 0, (cudaStream_t)stream>>>(
-        n, atm->T, atm->rho, atm->ne, pops, alpha, S, g->d_err);
-    RT_CUDA(cudaGetLastError());
-    return RT_OK;
+    return guarded([&]() -> rt_status {
+        RT_TRY(check_atmos(g, atm, pops));
+        if (!alpha || !S) return fail(RT_EINVAL, "null output");
+        RT_TRY(load_atom(atom));
+        const int64_t n = g->npt;
+        note_launch();
+        source_terms_kernel<<<(unsigned)((n + 127) / 128), 128, 0, (cudaStream_t)stream>>>(
+            n, atm->T, atm->rho, atm->ne, pops, alpha, S, g->d_err);
+        RT_CUDA(cudaGetLastError());
+        return RT_OK;
+    });
 }
 
 rt_status rt_source_terms_adjoint(rt_grid_t g, const rt_atom *atom, const rt_atmos *atm,
                                   const float *pops, const float *g_alpha, const float *g_S,
                                   float *g_T, void *stream)
 {
-    RT_TRY(check_atmos(g, atm, pops));
-    if (!g_alpha || !g_S || !g_T) return fail(RT_EINVAL, "null argument");
-    RT_TRY(load_atom(atom));
-    const int64_t n = g->npt;
-    note_launch();
-    source_terms_adjoint_kernel<<<(unsigned)((n + 127) / 128), 128, 0, (cudaStream_t)stream>>>(
-        n, atm->T, atm->rho, atm->ne, pops, g_alpha, g_S, g_T);
-    RT_CUDA(cudaGetLastError());
-    return RT_OK;
+    return guarded([&]() -> rt_status {
+        RT_TRY(check_atmos(g, atm, pops));
+        if (!g_alpha || !g_S || !g_T) return fail(RT_EINVAL, "null argument");
+        RT_TRY(load_atom(atom));
+        const int64_t n = g->npt;
+        note_launch();
+        source_terms_adjoint_kernel<<<(unsigned)((n + 127) / 128), 128, 0, (cudaStream_t)stream>>>(
+            n, atm->T, atm->rho, atm->ne, pops, g_alpha, g_S, g_T);
+        RT_CUDA(cudaGetLastError());
+        return RT_OK;
+    });
 }
 
 rt_status rt_lte_populations(rt_grid_t g, const rt_atom *atom, const rt_atmos *atm, float *pops,
                              void *stream)
 {
-    RT_TRY(check_atmos(g, atm, pops));
-    RT_TRY(load_atom(atom));
-    const int64_t n = g->npt;
-    note_launch();
-    lte_pops_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
-        n, atm->T, atm->ne, atm->nH, pops);
-    RT_CUDA(cudaGetLastError());
-    return RT_OK;
+    return guarded([&]() -> rt_status {
+        RT_TRY(check_atmos(g, atm, pops));
+        RT_TRY(load_atom(atom));
+        const int64_t n = g->npt;
+        note_launch();
+        lte_pops_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+            n, atm->T, atm->ne, atm->nH, pops);
+        RT_CUDA(cudaGetLastError());
+        return RT_OK;
+    });
 }
 
 rt_status rt_statistical_equilibrium(rt_grid_t g, const rt_atom *atom, const rt_atmos *atm,
                                      const float *J, float *pops, float *dmax_dev, void *stream)
 {
-    RT_TRY(check_atmos(g, atm, pops));
-    if (!J) return fail(RT_EINVAL, "null J");
-    RT_TRY(load_atom(atom));
-    const int64_t n = g->npt;
-    note_launch();
-    se_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
-        n, atm->T, atm->ne, atm->nH, J, pops, dmax_dev, g->d_err);
-    RT_CUDA(cudaGetLastError());
-    return RT_OK;
+    return guarded([&]() -> rt_status {
+        RT_TRY(check_atmos(g, atm, pops));
+        if (!J) return fail(RT_EINVAL, "null J");
+        RT_TRY(load_atom(atom));
+        const int64_t n = g->npt;
+        note_launch();
+        se_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+            n, atm->T, atm->ne, atm->nH, J, pops, dmax_dev, g->d_err);
+        RT_CUDA(cudaGetLastError());
+        return RT_OK;
+    });
 }
 
 rt_status rt_statistical_equilibrium_ali(rt_grid_t g, const rt_atom *atom, const rt_atmos *atm,
                                          const float *J, const float *Lstar, const float *S_old,
                                          float *pops, float *dmax_dev, int newton, void *stream)
 {
-    RT_TRY(check_atmos(g, atm, pops));
-    if (!J || !Lstar || !S_old) return fail(RT_EINVAL, "null J, Lstar or S_old");
-    if (newton < 0 || newton > 16) return fail(RT_EINVAL, "newton must be in 0..16");
-    if (atom->nlam > 64) return fail(RT_EINVAL, "the accelerated update takes at most 64 wavelengths");
-    RT_TRY(load_atom(atom));
-    const int64_t n = g->npt;
-    note_launch();
-    se_ali_kernel<<<ali_blocks(n), ALI_WARPS * 32, 0, (cudaStream_t)stream>>>(
-        n, atm->T, atm->rho, atm->ne, atm->nH, J, Lstar, S_old, pops, dmax_dev, g->d_err, newton);
-    RT_CUDA(cudaGetLastError());
-    return RT_OK;
+    return guarded([&]() -> rt_status {
+        RT_TRY(check_atmos(g, atm, pops));
+        if (!J || !Lstar || !S_old) return fail(RT_EINVAL, "null J, Lstar or S_old");
+        if (newton < 0 || newton > 16) return fail(RT_EINVAL, "newton must be in 0..16");
+        if (atom->nlam > 64) return fail(RT_EINVAL, "the accelerated update takes at most 64 wavelengths");
+        RT_TRY(load_atom(atom));
+        const int64_t n = g->npt;
+        note_launch();
+        se_ali_kernel<<<ali_blocks(n), ALI_WARPS * 32, 0, (cudaStream_t)stream>>>(
+            n, atm->T, atm->rho, atm->ne, atm->nH, J, Lstar, S_old, pops, dmax_dev, g->d_err, newton);
+        RT_CUDA(cudaGetLastError());
+        return RT_OK;
+    });
 }
 
 }  // extern "C"
@@ -1009,8 +1023,10 @@ rt_status rt_lambda_iterate(rt_grid_t g, const rt_atom *atom, const rt_atmos *at
                             int max_iter, double tol, int *iters_out, float *history,
                             int use_graph, void *stream)
 {
-    return iterate(g, atom, atm, pops, max_iter, tol, iters_out, history, use_graph, -1, 0, 0,
-                   stream);
+    return guarded([&]() -> rt_status {
+        return iterate(g, atom, atm, pops, max_iter, tol, iters_out, history, use_graph, -1, 0, 0,
+                       stream);
+    });
 }
 
 rt_status rt_lambda_iterate_ali(rt_grid_t g, const rt_atom *atom, const rt_atmos *atm,
@@ -1018,11 +1034,13 @@ rt_status rt_lambda_iterate_ali(rt_grid_t g, const rt_atom *atom, const rt_atmos
                                 float *history, int use_graph, int newton, int fixed_lstar,
                                 void *stream)
 {
-    if (newton < 0 || newton > 16) return fail(RT_EINVAL, "newton must be in 0..16");
-    if (atom && atom->nlam > 64)
-        return fail(RT_EINVAL, "the accelerated update takes at most 64 wavelengths");
-    return iterate(g, atom, atm, pops, max_iter, tol, iters_out, history, use_graph, newton,
-                   fixed_lstar, 0, stream);
+    return guarded([&]() -> rt_status {
+        if (newton < 0 || newton > 16) return fail(RT_EINVAL, "newton must be in 0..16");
+        if (atom && atom->nlam > 64)
+            return fail(RT_EINVAL, "the accelerated update takes at most 64 wavelengths");
+        return iterate(g, atom, atm, pops, max_iter, tol, iters_out, history, use_graph, newton,
+                       fixed_lstar, 0, stream);
+    });
 }
 
 rt_status rt_lambda_iterate_ex(rt_grid_t g, const rt_atom *atom, const rt_atmos *atm,
@@ -1030,12 +1048,14 @@ rt_status rt_lambda_iterate_ex(rt_grid_t g, const rt_atom *atom, const rt_atmos 
                                float *history, int use_graph, int newton, int fixed_lstar,
                                int ng_period, void *stream)
 {
-    if (newton < -1 || newton > 16) return fail(RT_EINVAL, "newton must be in -1..16");
-    if (ng_period < 0) return fail(RT_EINVAL, "ng_period must be >= 0");
-    if (newton >= 0 && atom && atom->nlam > 64)
-        return fail(RT_EINVAL, "the accelerated update takes at most 64 wavelengths");
-    return iterate(g, atom, atm, pops, max_iter, tol, iters_out, history, use_graph, newton,
-                   fixed_lstar, ng_period, stream);
+    return guarded([&]() -> rt_status {
+        if (newton < -1 || newton > 16) return fail(RT_EINVAL, "newton must be in -1..16");
+        if (ng_period < 0) return fail(RT_EINVAL, "ng_period must be >= 0");
+        if (newton >= 0 && atom && atom->nlam > 64)
+            return fail(RT_EINVAL, "the accelerated update takes at most 64 wavelengths");
+        return iterate(g, atom, atm, pops, max_iter, tol, iters_out, history, use_graph, newton,
+                       fixed_lstar, ng_period, stream);
+    });
 }
 
 // Host evaluation of the device Voigt function for testing: H(a, v) in FP32 arithmetic is not

@@ -121,84 +121,86 @@ extern "C" rt_status rt_formal_solution_regular_noalloc(
     const double *dirs, const double *wdir, int nlam, const float *alpha, const float *S, int bc,
     const float *I_bc, float *J, void *stream)
 {
-    if (nx < 1 || ny < 1 || nz < 2 || !(dx > 0) || !(dy > 0) || !z || ndir < 1 || !dirs ||
-        !wdir || nlam < 1 || nlam > 65535 || !alpha || !S || !J)
-        return fail(RT_EINVAL, "bad argument");
-    if (bc < RT_BC_THERMAL || bc > RT_BC_ARRAY || (bc == RT_BC_ARRAY && !I_bc))
-        return fail(RT_EINVAL, "bad boundary condition");
-    for (int k = 1; k < nz; ++k)
-        if (!(z[k] > z[k - 1])) return fail(RT_EINVAL, "z must be strictly ascending");
-    std::vector<int> hemi[2];
-    for (int q = 0; q < ndir; ++q) {
-        const double *u = dirs + 3 * q;
-        if (u[2] == 0.0) return fail(RT_EINVAL, "directions need mu_z != 0");
-        hemi[u[2] > 0 ? 0 : 1].push_back(q);
-    }
-    const size_t np = (size_t)nx * ny;
-    const size_t ndh = std::max(hemi[0].size(), hemi[1].size());
-    if (ndh > (size_t)NOALLOC_MAX_DH) return fail(RT_EINVAL, "at most 32 directions per hemisphere");
-    const size_t need = 2 * (size_t)nlam * ndh * np;
-    if (need > NOALLOC_SCRATCH_FLOATS)
-        return fail(RT_EINVAL, "problem exceeds the static scratch: 2 * nlam * (directions per "
-                               "hemisphere) * nx * ny must not exceed 4194304 floats");
-    float *scratch;
-    RT_TRY(noalloc_scratch(&scratch));
-    float *bufs[2] = {scratch, scratch + (size_t)nlam * ndh * np};
-    cudaStream_t st = (cudaStream_t)stream;
-    NoAllocPlane a;
-    a.alpha = alpha;
-    a.S = S;
-    a.J = J;
-    a.I_bc = I_bc;
-    a.nx = nx;
-    a.ny = ny;
-    a.nz = nz;
-    a.np = (int)np;
-    a.nlam = nlam;
-    a.periodic = periodic_xy ? 1 : 0;
-    a.bc = bc;
-    dim3 grid((unsigned)((np + 255) / 256), nlam);
-    int first = 1;
-    for (int h = 0; h < 2; ++h) {
-        if (hemi[h].empty()) continue;
-        a.up = h == 0;
-        a.first = first;
-        a.ndh = (int)hemi[h].size();
-        for (int d = 0; d < a.ndh; ++d) {
-            a.dg[d] = hemi[h][d];
-            a.w[d] = (float)wdir[hemi[h][d]];
+    return guarded([&]() -> rt_status {
+        if (nx < 1 || ny < 1 || nz < 2 || !(dx > 0) || !(dy > 0) || !z || ndir < 1 || !dirs ||
+            !wdir || nlam < 1 || nlam > 65535 || !alpha || !S || !J)
+            return fail(RT_EINVAL, "bad argument");
+        if (bc < RT_BC_THERMAL || bc > RT_BC_ARRAY || (bc == RT_BC_ARRAY && !I_bc))
+            return fail(RT_EINVAL, "bad boundary condition");
+        for (int k = 1; k < nz; ++k)
+            if (!(z[k] > z[k - 1])) return fail(RT_EINVAL, "z must be strictly ascending");
+        std::vector<int> hemi[2];
+        for (int q = 0; q < ndir; ++q) {
+            const double *u = dirs + 3 * q;
+            if (u[2] == 0.0) return fail(RT_EINVAL, "directions need mu_z != 0");
+            hemi[u[2] > 0 ? 0 : 1].push_back(q);
         }
-        for (int s = 0; s < nz; ++s) {
-            const int k = a.up ? s : nz - 1 - s;
-            if (s > 0) {
-                const int ku = a.up ? k - 1 : k + 1;
-                for (int d = 0; d < a.ndh; ++d) {
-                    const double *u = dirs + 3 * hemi[h][d];
-                    const double ds = std::fabs(z[k] - z[ku]) / std::fabs(u[2]);
-                    const double cx = -ds * u[0] / dx, cy = -ds * u[1] / dy;
-                    const double fx = std::floor(cx), fy = std::floor(cy);
-                    const double tx = cx - fx, ty = cy - fy;
-                    Stencil &sc = a.st[d];
-                    sc.ax = (int)fx;
-                    sc.ay = (int)fy;
-                    sc.axm = ((sc.ax % nx) + nx) % nx;
-                    sc.aym = ((sc.ay % ny) + ny) % ny;
-                    sc.w0 = (float)((1.0 - tx) * (1.0 - ty));
-                    sc.w1 = (float)(tx * (1.0 - ty));
-                    sc.w2 = (float)((1.0 - tx) * ty);
-                    sc.w3 = (float)(tx * ty);
-                    sc.hds = (float)(0.5 * ds);
-                    sc.pad = 0.f;
-                }
+        const size_t np = (size_t)nx * ny;
+        const size_t ndh = std::max(hemi[0].size(), hemi[1].size());
+        if (ndh > (size_t)NOALLOC_MAX_DH) return fail(RT_EINVAL, "at most 32 directions per hemisphere");
+        const size_t need = 2 * (size_t)nlam * ndh * np;
+        if (need > NOALLOC_SCRATCH_FLOATS)
+            return fail(RT_EINVAL, "problem exceeds the static scratch: 2 * nlam * (directions per "
+                                   "hemisphere) * nx * ny must not exceed 4194304 floats");
+        float *scratch;
+        RT_TRY(noalloc_scratch(&scratch));
+        float *bufs[2] = {scratch, scratch + (size_t)nlam * ndh * np};
+        cudaStream_t st = (cudaStream_t)stream;
+        NoAllocPlane a;
+        a.alpha = alpha;
+        a.S = S;
+        a.J = J;
+        a.I_bc = I_bc;
+        a.nx = nx;
+        a.ny = ny;
+        a.nz = nz;
+        a.np = (int)np;
+        a.nlam = nlam;
+        a.periodic = periodic_xy ? 1 : 0;
+        a.bc = bc;
+        dim3 grid((unsigned)((np + 255) / 256), nlam);
+        int first = 1;
+        for (int h = 0; h < 2; ++h) {
+            if (hemi[h].empty()) continue;
+            a.up = h == 0;
+            a.first = first;
+            a.ndh = (int)hemi[h].size();
+            for (int d = 0; d < a.ndh; ++d) {
+                a.dg[d] = hemi[h][d];
+                a.w[d] = (float)wdir[hemi[h][d]];
             }
-            a.step = s;
-            a.Iprev = bufs[(s + 1) & 1];
-            a.Inext = bufs[s & 1];
-            note_launch();
-            sc_plane_noalloc_kernel<<<grid, 256, 0, st>>>(a);
+            for (int s = 0; s < nz; ++s) {
+                const int k = a.up ? s : nz - 1 - s;
+                if (s > 0) {
+                    const int ku = a.up ? k - 1 : k + 1;
+                    for (int d = 0; d < a.ndh; ++d) {
+                        const double *u = dirs + 3 * hemi[h][d];
+                        const double ds = std::fabs(z[k] - z[ku]) / std::fabs(u[2]);
+                        const double cx = -ds * u[0] / dx, cy = -ds * u[1] / dy;
+                        const double fx = std::floor(cx), fy = std::floor(cy);
+                        const double tx = cx - fx, ty = cy - fy;
+                        Stencil &sc = a.st[d];
+                        sc.ax = (int)fx;
+                        sc.ay = (int)fy;
+                        sc.axm = ((sc.ax % nx) + nx) % nx;
+                        sc.aym = ((sc.ay % ny) + ny) % ny;
+                        sc.w0 = (float)((1.0 - tx) * (1.0 - ty));
+                        sc.w1 = (float)(tx * (1.0 - ty));
+                        sc.w2 = (float)((1.0 - tx) * ty);
+                        sc.w3 = (float)(tx * ty);
+                        sc.hds = (float)(0.5 * ds);
+                        sc.pad = 0.f;
+                    }
+                }
+                a.step = s;
+                a.Iprev = bufs[(s + 1) & 1];
+                a.Inext = bufs[s & 1];
+                note_launch();
+                sc_plane_noalloc_kernel<<<grid, 256, 0, st>>>(a);
+            }
+            first = 0;
         }
-        first = 0;
-    }
-    RT_CUDA(cudaGetLastError());
-    return RT_OK;
+        RT_CUDA(cudaGetLastError());
+        return RT_OK;
+    });
 }

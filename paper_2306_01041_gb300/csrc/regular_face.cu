@@ -484,14 +484,16 @@ using namespace rt;
 
 extern "C" rt_status rt_grid_set_scheme(rt_grid_t g, int scheme)
 {
-    if (!g) return fail(RT_EINVAL, "null grid");
-    if (scheme != RT_SC_PLANE && scheme != RT_SC_FACE) return fail(RT_EINVAL, "unknown scheme");
-    if (scheme == RT_SC_FACE) {
-        if (g->kind != RT_GRID_REGULAR) return fail(RT_EINVAL, "the face scheme is for regular grids");
-        if (!g->periodic) return fail(RT_EINVAL, "the face scheme needs periodic sides");
-        if (std::max(g->nx, g->ny) > FACE_MAXNB) return fail(RT_EINVAL, "face scheme: nx, ny <= 256");
-        if (!g->face) RT_TRY(face_build(g));
-    }
-    g->sc_face = scheme == RT_SC_FACE;
-    return RT_OK;
+    return guarded([&]() -> rt_status {
+        if (!g) return fail(RT_EINVAL, "null grid");
+        if (scheme != RT_SC_PLANE && scheme != RT_SC_FACE) return fail(RT_EINVAL, "unknown scheme");
+        if (scheme == RT_SC_FACE) {
+            if (g->kind != RT_GRID_REGULAR) return fail(RT_EINVAL, "the face scheme is for regular grids");
+            if (!g->periodic) return fail(RT_EINVAL, "the face scheme needs periodic sides");
+            if (std::max(g->nx, g->ny) > FACE_MAXNB) return fail(RT_EINVAL, "face scheme: nx, ny <= 256");
+            if (!g->face) RT_TRY(face_build(g));
+        }
+        g->sc_face = scheme == RT_SC_FACE;
+        return RT_OK;
+    });
 }

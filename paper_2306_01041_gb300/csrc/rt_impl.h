@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <exception>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -24,6 +26,22 @@ rt_status cuda_fail(cudaError_t e, const char *what);
         rt_status s_ = (call);                                        \
         if (s_ != RT_OK) return s_;                                   \
     } while (0)
+
+// The body of a C ABI entry point: a failed host allocation or any other C++ exception becomes a
+// status (and a message) instead of crossing the C boundary.
+template <class F>
+rt_status guarded(F &&body)
+{
+    try {
+        return body();
+    } catch (const std::bad_alloc &) {
+        return fail(RT_ENOMEM, "host allocation failed");
+    } catch (const std::exception &e) {
+        return fail(RT_EINVAL, e.what());
+    } catch (...) {
+        return fail(RT_EINVAL, "unexpected host exception");
+    }
+}
 
 // process-wide count of kernel launches issued by the library (also those recorded into a graph)
 void note_launch(unsigned n = 1);

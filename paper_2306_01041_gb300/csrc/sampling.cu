@@ -218,78 +218,80 @@ extern "C" rt_status rt_sample_sites(int nx, int ny, int nz, const double *z, co
                                      const float *f, int64_t nsites, uint64_t seed, double *xyz,
                                      int64_t *nproposals, void *stream)
 {
-    if (nx < 1 || ny < 1 || nz < 2 || !z || !box || !f || nsites < 1 || !xyz)
-        return fail(RT_EINVAL, "sample_sites: bad argument");
-    if ((int64_t)nx * ny * nz > ((int64_t)1 << 40)) return fail(RT_EINVAL, "mesh too large");
-    for (int k = 1; k < nz; ++k)
-        if (!(z[k] > z[k - 1])) return fail(RT_EINVAL, "z must be strictly ascending");
-    if (!(box[1] > box[0] && box[3] > box[2] && box[5] > box[4]))
-        return fail(RT_EINVAL, "box must have positive extent");
-    if ((uintptr_t)xyz % 8) return fail(RT_EINVAL, "xyz must be 8-byte aligned");
-    cudaStream_t st = (cudaStream_t)stream;
-    const size_t n = (size_t)nx * ny * nz;
-    // device scratch: z, counts, offsets, sum, last, fmax bits, bad flag
-    struct Buf {
-        void *p = nullptr;
-        ~Buf() { if (p) cudaFree(p); }
-    } buf;
-    const size_t zb = (size_t)nz * sizeof(double);
-    const size_t bytes = zb + 2 * SMP_BLOCKS * sizeof(int) + 64;
-    RT_CUDA(cudaMalloc(&buf.p, bytes));
-    double *dz = (double *)buf.p;
-    int *counts = (int *)((char *)buf.p + zb);
-    int *offsets = counts + SMP_BLOCKS;
-    int *sum = offsets + SMP_BLOCKS;
-    unsigned long long *last = (unsigned long long *)(((uintptr_t)(sum + 1) + 7) & ~(uintptr_t)7);
-    unsigned *fmax_bits = (unsigned *)(last + 1);
-    unsigned *bad = fmax_bits + 1;
-    RT_CUDA(cudaMemcpyAsync(dz, z, zb, cudaMemcpyHostToDevice, st));
-    RT_CUDA(cudaMemsetAsync(fmax_bits, 0, 2 * sizeof(unsigned), st));
-    note_launch();
-    sample_check_kernel<<<1216, 256, 0, st>>>(f, n, fmax_bits, bad);
-    unsigned h[2];
-    RT_CUDA(cudaMemcpyAsync(h, fmax_bits, sizeof(h), cudaMemcpyDeviceToHost, st));
-    RT_CUDA(cudaStreamSynchronize(st));
-    float fmax;
-    std::memcpy(&fmax, &h[0], sizeof(float));
-    if (h[1]) return fail(RT_EINVAL, "sample_sites: target must be finite and non-negative");
-    if (!(fmax > 0.f)) return fail(RT_EINVAL, "sample_sites: target is zero everywhere");
-    SampleArgs a;
-    a.f = f;
-    a.z = dz;
-    for (int c = 0; c < 6; ++c) a.box[c] = box[c];
-    a.fmax = (double)fmax;
-    a.seed = seed;
-    a.nx = nx;
-    a.ny = ny;
-    a.nz = nz;
-    const uint64_t max_prop = 1000ull * (uint64_t)nsites + (1ull << 20);
-    int64_t have = 0;
-    uint64_t base = 0;
-    unsigned long long h_last = 0;
-    while (have < nsites) {
-        if (base >= max_prop)
-            return fail(RT_ENOCONV, "sample_sites: too few proposals accepted");
-        note_launch(2);
-        sample_count_kernel<<<SMP_BLOCKS, SMP_THREADS, 0, st>>>(a, base, counts);
-        sample_offsets_kernel<<<1, SMP_BLOCKS, 0, st>>>(counts, offsets, sum);
-        int h_sum = 0;
-        RT_CUDA(cudaMemcpyAsync(&h_sum, sum, sizeof(int), cudaMemcpyDeviceToHost, st));
+    return guarded([&]() -> rt_status {
+        if (nx < 1 || ny < 1 || nz < 2 || !z || !box || !f || nsites < 1 || !xyz)
+            return fail(RT_EINVAL, "sample_sites: bad argument");
+        if ((int64_t)nx * ny * nz > ((int64_t)1 << 40)) return fail(RT_EINVAL, "mesh too large");
+        for (int k = 1; k < nz; ++k)
+            if (!(z[k] > z[k - 1])) return fail(RT_EINVAL, "z must be strictly ascending");
+        if (!(box[1] > box[0] && box[3] > box[2] && box[5] > box[4]))
+            return fail(RT_EINVAL, "box must have positive extent");
+        if ((uintptr_t)xyz % 8) return fail(RT_EINVAL, "xyz must be 8-byte aligned");
+        cudaStream_t st = (cudaStream_t)stream;
+        const size_t n = (size_t)nx * ny * nz;
+        // device scratch: z, counts, offsets, sum, last, fmax bits, bad flag
+        struct Buf {
+            void *p = nullptr;
+            ~Buf() { if (p) cudaFree(p); }
+        } buf;
+        const size_t zb = (size_t)nz * sizeof(double);
+        const size_t bytes = zb + 2 * SMP_BLOCKS * sizeof(int) + 64;
+        RT_CUDA(cudaMalloc(&buf.p, bytes));
+        double *dz = (double *)buf.p;
+        int *counts = (int *)((char *)buf.p + zb);
+        int *offsets = counts + SMP_BLOCKS;
+        int *sum = offsets + SMP_BLOCKS;
+        unsigned long long *last = (unsigned long long *)(((uintptr_t)(sum + 1) + 7) & ~(uintptr_t)7);
+        unsigned *fmax_bits = (unsigned *)(last + 1);
+        unsigned *bad = fmax_bits + 1;
+        RT_CUDA(cudaMemcpyAsync(dz, z, zb, cudaMemcpyHostToDevice, st));
+        RT_CUDA(cudaMemsetAsync(fmax_bits, 0, 2 * sizeof(unsigned), st));
+        note_launch();
+        sample_check_kernel<<<1216, 256, 0, st>>>(f, n, fmax_bits, bad);
+        unsigned h[2];
+        RT_CUDA(cudaMemcpyAsync(h, fmax_bits, sizeof(h), cudaMemcpyDeviceToHost, st));
         RT_CUDA(cudaStreamSynchronize(st));
-        if (h_sum > 0) {
-            const int64_t need = nsites - have;
-            note_launch();
-            sample_write_kernel<<<SMP_BLOCKS, SMP_THREADS, 0, st>>>(a, base, offsets, have, need,
-                                                                  xyz, last);
-            RT_CUDA(cudaGetLastError());
-            if (h_sum >= need) {
-                RT_CUDA(cudaMemcpyAsync(&h_last, last, sizeof(h_last), cudaMemcpyDeviceToHost, st));
-                RT_CUDA(cudaStreamSynchronize(st));
+        float fmax;
+        std::memcpy(&fmax, &h[0], sizeof(float));
+        if (h[1]) return fail(RT_EINVAL, "sample_sites: target must be finite and non-negative");
+        if (!(fmax > 0.f)) return fail(RT_EINVAL, "sample_sites: target is zero everywhere");
+        SampleArgs a;
+        a.f = f;
+        a.z = dz;
+        for (int c = 0; c < 6; ++c) a.box[c] = box[c];
+        a.fmax = (double)fmax;
+        a.seed = seed;
+        a.nx = nx;
+        a.ny = ny;
+        a.nz = nz;
+        const uint64_t max_prop = 1000ull * (uint64_t)nsites + (1ull << 20);
+        int64_t have = 0;
+        uint64_t base = 0;
+        unsigned long long h_last = 0;
+        while (have < nsites) {
+            if (base >= max_prop)
+                return fail(RT_ENOCONV, "sample_sites: too few proposals accepted");
+            note_launch(2);
+            sample_count_kernel<<<SMP_BLOCKS, SMP_THREADS, 0, st>>>(a, base, counts);
+            sample_offsets_kernel<<<1, SMP_BLOCKS, 0, st>>>(counts, offsets, sum);
+            int h_sum = 0;
+            RT_CUDA(cudaMemcpyAsync(&h_sum, sum, sizeof(int), cudaMemcpyDeviceToHost, st));
+            RT_CUDA(cudaStreamSynchronize(st));
+            if (h_sum > 0) {
+                const int64_t need = nsites - have;
+                note_launch();
+                sample_write_kernel<<<SMP_BLOCKS, SMP_THREADS, 0, st>>>(a, base, offsets, have, need,
+                                                                      xyz, last);
+                RT_CUDA(cudaGetLastError());
+                if (h_sum >= need) {
+                    RT_CUDA(cudaMemcpyAsync(&h_last, last, sizeof(h_last), cudaMemcpyDeviceToHost, st));
+                    RT_CUDA(cudaStreamSynchronize(st));
+                }
+                have += std::min<int64_t>(h_sum, need);
             }
-            have += std::min<int64_t>(h_sum, need);
+            base += SMP_BATCH;
         }
-        base += SMP_BATCH;
-    }
-    if (nproposals) *nproposals = (int64_t)h_last;
-    return RT_OK;
+        if (nproposals) *nproposals = (int64_t)h_last;
+        return RT_OK;
+    });
 }
