@@ -105,6 +105,15 @@ rt_status rt_grid_info(rt_grid_t grid, int64_t *npt, int64_t *ntop, int *max_lev
  * len[ndir][nsites][2] (metres), level[ndir][nsites].  Voronoi grids only.  Synchronous. */
 rt_status rt_grid_tables(rt_grid_t grid, int32_t *k, float *w, float *len, int32_t *level);
 
+/* Rebuilds a Voronoi grid's upwind tables and dependency levels on the GPU: the definition of
+ * rt_grid_create's host build (two best-aligned upwind neighbours, weights v^r / sum v^r,
+ * segment lengths, levels), every geometric step one IEEE double operation in the same order, so
+ * the choices are the host build's; the levels come from relaxation passes over the links.  The
+ * new tables replace the grid's in place (same device arrays, so batches made from the grid stay
+ * valid); rt_grid_tables and rt_grid_info then report them.  Synchronous; allocates and frees a
+ * device buffer the size of the neighbour lists and the tables.  RT_EINVAL for a regular grid. */
+rt_status rt_grid_build_tables_device(rt_grid_t grid, void *stream);
+
 /* Emergent-layer point indices (host array of ntop entries). */
 rt_status rt_grid_top_points(rt_grid_t grid, int64_t *idx);
 

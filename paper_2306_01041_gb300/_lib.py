@@ -63,6 +63,7 @@ SIGNATURES = {
     "rt_grid_tables": (c_int, [P, PI32, PF, PF, PI32]),
     "rt_grid_top_points": (c_int, [P, PI64]),
     "rt_grid_set_scheme": (c_int, [P, c_int]),
+    "rt_grid_build_tables_device": (c_int, [P, P]),
     "rt_formal_solution": (c_int, [P, c_int, P, P, c_int, P, P, P, P]),
     "rt_source_terms_lte": (c_int, [c_int64, P, P, c_double, c_double, P, P, P]),
     "rt_source_terms_lte_adjoint": (c_int, [c_int64, P, P, c_double, c_double, P, P, P, P]),

@@ -71,6 +71,15 @@ class Grid:
         self.scheme = scheme
         return self
 
+    def build_tables_device(self, stream=None):
+        """Rebuild a Voronoi grid's upwind tables and levels on the GPU (in place)."""
+        check(lib().rt_grid_build_tables_device(self._h, _stream(stream)))
+        npt, ntop, ml, nfb = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int(), ctypes.c_int64()
+        check(lib().rt_grid_info(self._h, ctypes.byref(npt), ctypes.byref(ntop), ctypes.byref(ml),
+                                 ctypes.byref(nfb)))
+        self.max_levels, self.n_fallback = ml.value, nfb.value
+        return self
+
     def top_points(self):
         out = np.empty(self.ntop, np.int64)
         check(lib().rt_grid_top_points(self._h, out.ctypes.data_as(L.PI64)))

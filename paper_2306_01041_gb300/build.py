@@ -13,7 +13,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "librt.so")
 SOURCES = ["api.cu", "regular.cu", "regular_tile.cu", "regular_cluster.cu", "voronoi.cu",
            "nlte.cu", "batch.cu", "noalloc.cu", "ali.cu", "idw.cu", "ng.cu",
-           "regular_face.cu", "sampling.cu"]
+           "regular_face.cu", "sampling.cu", "tables.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fopenmp,-O3",
          "-Xptxas", "-warn-spills"]

@@ -320,7 +320,15 @@ rt_status voronoi_build_tables(const rt_grid *g, int nd, const double *dirs, Vor
                             &vt.h_level[(size_t)q * n]))
             return fail(RT_ECYCLE, "upwind links are not acyclic");
     }
-    // slots: sites of each direction in level order (stable by site index within a level)
+    return voronoi_upload_slots(vt, n, st);
+}
+
+// Slots: the sites of each direction in level order (stable by site index within a level), from
+// vt.h_up and vt.h_level; sets the level offsets and max_levels and uploads the slot-ordered
+// records and the slot -> site map (into the existing device arrays when there are some).
+rt_status voronoi_upload_slots(VorTables &vt, int64_t n, cudaStream_t st)
+{
+    const int nd = vt.ndir;
     std::vector<Upwind> slot_up((size_t)nd * n);
     std::vector<int32_t> order((size_t)nd * n);
     vt.lvl_off.assign(nd, {});
@@ -341,8 +349,8 @@ rt_status voronoi_build_tables(const rt_grid *g, int nd, const double *dirs, Vor
         }
         vt.max_levels = std::max(vt.max_levels, L);
     }
-    RT_CUDA(cudaMalloc(&vt.d_up, slot_up.size() * sizeof(Upwind)));
-    RT_CUDA(cudaMalloc(&vt.d_order, order.size() * sizeof(int32_t)));
+    if (!vt.d_up) RT_CUDA(cudaMalloc(&vt.d_up, slot_up.size() * sizeof(Upwind)));
+    if (!vt.d_order) RT_CUDA(cudaMalloc(&vt.d_order, order.size() * sizeof(int32_t)));
     RT_CUDA(cudaMemcpyAsync(vt.d_up, slot_up.data(), slot_up.size() * sizeof(Upwind),
                             cudaMemcpyHostToDevice, st));
     RT_CUDA(cudaMemcpyAsync(vt.d_order, order.data(), order.size() * sizeof(int32_t),

@@ -168,6 +168,8 @@ rt_status regular_formal_solution(rt_grid *g, int nlam, const float *alpha, cons
 rt_status face_formal_solution(rt_grid *g, int nlam, const float *alpha, const float *S, int bc,
                                const float *I_bc, float *J, float *I_dir, cudaStream_t st);
 rt_status face_prepare(rt_grid *g, int nlam);
+// Voronoi tables: slot order, level offsets and upload from vt.h_up and vt.h_level
+rt_status voronoi_upload_slots(VorTables &vt, int64_t n, cudaStream_t st);
 // fused cluster sweep over all planes; *done = false when it does not apply to this grid
 rt_status regular_cluster_sweep(rt_grid *g, int nlam, const float *alpha, const float *S, int bc,
                                 float *J, cudaStream_t st, bool *done);

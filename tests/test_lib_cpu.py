@@ -132,12 +132,14 @@ def test_accelerated_and_synthesis_entry_points_reject_bad_arguments_on_host(lib
 
 
 def test_face_scheme_and_site_sampling_reject_bad_arguments_on_host(librt):
-    """rt_grid_set_scheme and rt_sample_sites validate on the host before any device work."""
+    """rt_grid_set_scheme, rt_grid_build_tables_device and rt_sample_sites validate on the host
+    before any device work."""
     import paper_2306_01041_gb300 as rt
     from paper_2306_01041_gb300 import _lib as L
     lib = rt.lib()
     n0 = rt.kernel_launches()
     assert lib.rt_grid_set_scheme(None, L.RT_SC_FACE) == L.RT_EINVAL
+    assert lib.rt_grid_build_tables_device(None, None) == L.RT_EINVAL
     z = np.linspace(0.0, 1.0, 4)
     box = np.array([0.0, 1.0, 0.0, 1.0, 0.0, 1.0])
     fake = ctypes.c_void_p(256)                     # never dereferenced: rejected first
