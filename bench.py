@@ -583,6 +583,33 @@ def run_sample(args):
                       "msites_s": round(n / ms / 1e3, 3)}))
 
 
+def run_tables(args):
+    """Voronoi upwind tables and levels: the host build inside rt_grid_create against the GPU
+    rebuild (rt_grid_build_tables_device), on an atmosphere grid of args.tables sites."""
+    import torch
+    import paper_2306_01041_gb300 as rt
+    from synth import s4_quadrature
+    _, g, _, _ = _make_vor((1, args.tables))
+    dirs, w = s4_quadrature()
+    mk = lambda: rt.VoronoiGrid(g["xyz"], g["nbr_off"], g["nbr_idx"], g["nbr_shift"],  # noqa: E731
+                                g["box"], dirs, w)
+    mk()
+    torch.cuda.synchronize()
+    host, dev = [], []
+    for _ in range(max(1, args.steps)):
+        t0 = time.perf_counter()
+        G = mk()
+        host.append(time.perf_counter() - t0)
+        t0 = time.perf_counter()
+        G.build_tables_device()
+        dev.append(time.perf_counter() - t0)
+    print(json.dumps({"workload": f"Voronoi upwind tables and levels, {args.tables} sites, "
+                                  f"{len(dirs)} directions",
+                      "grid_create_with_host_tables_ms": round(statistics.median(host) * 1e3, 2),
+                      "device_rebuild_ms": round(statistics.median(dev) * 1e3, 2),
+                      "max_levels": G.max_levels}))
+
+
 def run_voronoi_batch(args):
     """The batched Voronoi formal solution alone on the first N atmospheres of the 8-atmosphere
     workload (52 wavelengths, 24 directions, populations at LTE): a smaller case of the batched
@@ -756,6 +783,8 @@ def main():
     ap.add_argument("--max-iter", type=int, default=300)
     ap.add_argument("--ng", type=int, default=0, help="Ng extrapolation period (0: off)")
     ap.add_argument("--tol", type=float, default=1e-3)
+    ap.add_argument("--tables", type=int, default=0,
+                    help="time the Voronoi table build (host and GPU) on a grid of this many sites")
     ap.add_argument("--sample", type=int, default=0,
                     help="time only the rejection sampling of this many Voronoi sites")
     ap.add_argument("--scheme", choices=["plane", "face"], default="plane",
@@ -779,6 +808,9 @@ def main():
         return
     if args.sample:
         run_sample(args)
+        return
+    if args.tables:
+        run_tables(args)
         return
     if args.iterate:
         run_iterate(args)
