@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
-from helpers import assert_parity, to_gpu, voronoi_grid
+from helpers import assert_parity, lattice_grid, tie_directions, to_gpu, voronoi_grid
 from synth import delaunay_neighbours, s4_quadrature
 
 pytestmark = pytest.mark.gpu
@@ -29,8 +29,9 @@ def _unit_box(seed=1, n=400):
     return dict(xyz=xyz, nbr_off=off, nbr_idx=code, nbr_shift=shift, box=box)
 
 
-def _check(rt, g):
-    dirs, w = s4_quadrature()
+def _check(rt, g, dirs=None, w=None):
+    if dirs is None:
+        dirs, w = s4_quadrature()
     G = rt.VoronoiGrid(g["xyz"], g["nbr_off"], g["nbr_idx"], g["nbr_shift"], g["box"], dirs, w)
     host = G.tables()
     ml, nfb = G.max_levels, G.n_fallback
@@ -51,6 +52,14 @@ def _check(rt, g):
 
 def test_unit_box_grid(rt):
     _check(rt, _unit_box())
+
+
+def test_lattice_grid_with_exact_ties(rt):
+    """Two neighbours tie exactly for second place for every direction: the tie rules decide (by
+    neighbour code on the lattice); in a one-site-wide column every lateral neighbour is a periodic
+    image of the site above or below."""
+    _check(rt, lattice_grid(4), *tie_directions())
+    _check(rt, lattice_grid(1, 4), *tie_directions())
 
 
 def test_atmosphere_grid_and_formal_solution(rt):
