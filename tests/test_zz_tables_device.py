@@ -64,7 +64,7 @@ def test_lattice_grid_with_exact_ties(rt):
 
 def test_atmosphere_grid_and_formal_solution(rt):
     """A 3000-site grid sampled from |dtau/dz| of the synthetic atmosphere; the formal solution
-    of three wavelengths on the rebuilt tables against the oracle, every boundary condition."""
+    of three wavelengths on the rebuilt tables against the oracle, thermal and zero inflow."""
     atm, g, f = voronoi_grid(3000, "dtau", 4)
     G, dirs, w, tab = _check(rt, g)
     rng = np.random.default_rng(5)
