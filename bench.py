@@ -29,6 +29,7 @@ sys.path.insert(0, ROOT)
 
 NX = NY = NZ = 128
 NDIR = 24
+SCHEME = "plane"          # regular-grid short characteristics: "plane" or "face"
 WORKLOAD = "NLTE Lambda iteration, regular grid 128x128x128, 52 wavelengths, 24 directions"
 
 # DRAM bytes per launch of the dominant kernel from the ncu capture summarised in profiles/,
@@ -336,18 +337,22 @@ def _cpu_inputs():
 
 def cpu_baseline(nl):
     """The oracle as it stands on this host's cores: the formal solution (sweep + J) of nl of the
-    52 wavelengths on the same 128^3 grid, which is the dominant cost of the step."""
+    52 wavelengths on the benchmark's grid (with the benchmark's scheme), the dominant cost of the
+    step."""
     import oracle
     c = _cpu_inputs()
     alpha, S, dx, dy, z, dirs, w = (c[k] for k in ("alpha", "S", "dx", "dy", "z", "dirs", "w"))
     pick = np.linspace(0, alpha.shape[0] - 1, nl).astype(int)
+    sweep = oracle.sc_regular_face if SCHEME == "face" else oracle.sc_regular
     t = time.perf_counter()
-    oracle.sc_regular(NX, NY, NZ, dx, dy, z, dirs, w, alpha[pick], S[pick])
+    sweep(NX, NY, NZ, dx, dy, z, dirs, w, alpha[pick], S[pick])
     dt = time.perf_counter() - t
     upd = NX * NY * NZ * NDIR * nl
+    scheme = ", face-hitting" if SCHEME == "face" else ""
     return {"value": round(upd / dt / 1e9, 5), "unit": "Gupd/s", "cores": oracle.num_threads(),
             "kind": "oracle", "seconds": round(dt, 2),
-            "sample": f"formal solution of {nl} of 52 wavelengths, 128^3 grid, 24 directions"}
+            "sample": f"formal solution of {nl} of 52 wavelengths, {NX}x{NY}x{NZ} grid, "
+                      f"24 directions{scheme}"}
 
 
 def run_reference(args):
@@ -793,12 +798,13 @@ def main():
     ap.add_argument("--z-stretch", type=float, default=0.0,
                     help="non-uniform z spacing amplitude a in [0, 1) (cell heights (1 -+ a) dz)")
     args = ap.parse_args()
-    global NX, NY, NZ, WORKLOAD
+    global NX, NY, NZ, WORKLOAD, SCHEME
     if args.nx != 128:
         NX = NY = NZ = args.nx
         WORKLOAD = WORKLOAD.replace("128x128x128", f"{NX}x{NY}x{NZ}")
     if args.z_stretch:
         WORKLOAD += f", stretched z (a = {args.z_stretch})"
+    SCHEME = args.scheme
     if args.scheme == "face":
         WORKLOAD += ", face-hitting short characteristics"
     if args.warmup < 3:
