@@ -323,6 +323,20 @@ rt_status rt_batch_formal_solution(rt_batch_t batch, const float *const *alpha,
                                    const float *const *S, int bc, float *const *J,
                                    void *stream);
 
+/* Lambda iteration (Sect. 2.1, Eq. 3-4) of every atmosphere of the batch together: per iteration
+ * the source terms of each atmosphere, one batched formal solution of all of them (RT_BC_THERMAL),
+ * and the rates and statistical equilibrium of each, until the largest relative population change
+ * over every atmosphere is below tol or max_iter iterations have run (RT_ENOCONV then).  One model
+ * atom serves the whole batch (atom->nlam must equal the batch's nlam); atms[b] (host array of
+ * ngrids descriptions of device fields) and pops[b] (host array of ngrids device pointers, each
+ * [3][npt_b], in = start, out = last iterate) per atmosphere.  iters_out, history as for
+ * rt_lambda_iterate.  use_graph != 0 captures one iteration of the whole batch in a CUDA graph and
+ * replays it.  Uses each grid's iteration scratch (allocated on first use); synchronises once per
+ * iteration to read the convergence scalar. */
+rt_status rt_batch_lambda_iterate(rt_batch_t batch, const rt_atom *atom, const rt_atmos *atms,
+                                  float *const *pops, int max_iter, double tol, int *iters_out,
+                                  float *history, int use_graph, void *stream);
+
 /* ---- site sampling (Sect. 2.4) -------------------------------------------------------------
  * Rejection sampling of Voronoi sites: proposals uniform in the box are kept where the target f is
  * at least a uniform rejection level times max f, until nsites are kept.  Proposal p = 0, 1, 2, ...
@@ -356,11 +370,16 @@ rt_status rt_sample_sites(int nx, int ny, int nz, const double *z, const double 
  * overwritten; I_bc: device [ndir][nlam][nx*ny] for RT_BC_ARRAY, else NULL.
  * Limits: 2 * nlam * (directions per hemisphere) * nx * ny <= 4194304 floats, at most 32
  * directions per hemisphere; larger problems return RT_EINVAL with a message, before any device
- * work.  The first call on a device looks up the array's device address (cudaGetSymbolAddress,
- * with that device current); make that first call before any stream capture.  All calls share
- * the one array, which keeps the last call's contents (nothing in it needs to start at zero):
- * calls that overlap on the GPU -- on different streams, or from different host threads --
- * race on it and must be serialised by the caller.  Asynchronous on `stream`. */
+ * work.  Every call looks up the array's device address in the CUDA context current on the
+ * calling thread (cudaGetSymbolAddress, which allocates nothing), so it works in the runtime's
+ * primary context, in a context the host application created, and after cudaDeviceReset.  The
+ * first call in a context may load the library's device code and reserve the 16 MiB array there
+ * (with lazy module loading this happens at that call, not when the library is loaded), and can
+ * fail with RT_ECUDA under a device-memory budget that has no room left; make that first call
+ * before any stream capture.  All calls share the one array, which keeps the last call's contents
+ * (nothing in it needs to start at zero): calls that overlap on the GPU -- on different streams,
+ * or from different host threads -- race on it and must be serialised by the caller.
+ * Asynchronous on `stream`. */
 rt_status rt_formal_solution_regular_noalloc(int nx, int ny, int nz, double dx, double dy,
                                              const double *z, int periodic_xy, int ndir,
                                              const double *dirs, const double *wdir, int nlam,

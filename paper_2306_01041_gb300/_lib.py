@@ -99,6 +99,9 @@ SIGNATURES = {
     "rt_batch_destroy": (None, [P]),
     "rt_batch_formal_solution": (c_int, [P, ctypes.POINTER(P), ctypes.POINTER(P), c_int,
                                          ctypes.POINTER(P), P]),
+    "rt_batch_lambda_iterate": (c_int, [P, ctypes.POINTER(AtomDesc), ctypes.POINTER(AtmosDesc),
+                                        ctypes.POINTER(P), c_int, c_double, ctypes.POINTER(c_int),
+                                        PF, c_int, P]),
     "rt_sample_sites": (c_int, [c_int, c_int, c_int, PD, PD, P, c_int64, ctypes.c_uint64, P,
                                 PI64, P]),
     "rt_last_error": (ctypes.c_char_p, []),

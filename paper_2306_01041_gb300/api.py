@@ -478,3 +478,23 @@ class Batch:
         pj = (ctypes.c_void_p * n)(*[_dev(j).value for j in Js])
         check(lib().rt_batch_formal_solution(self._h, pa, ps, bc, pj, _stream(stream)))
         return Js
+
+    def lambda_iterate(self, atom: Atom, atms, pops, max_iter=300, tol=1e-3, use_graph=True,
+                       stream=None):
+        """Lambda iteration of every atmosphere of the batch together (one model atom), in place on
+        pops (one [3][npt] tensor per grid); returns (iterations, history, converged)."""
+        n = len(self.grids)
+        if len(atms) != n or len(pops) != n:
+            raise ValueError("one Atmos and one pops tensor per grid")
+        descs = (L.AtmosDesc * n)(*[m.desc for m in atms])
+        pp = (ctypes.c_void_p * n)(*[_dev(p, (3, g.npt), "pops").value
+                                     for p, g in zip(pops, self.grids)])
+        hist = np.zeros(max_iter, np.float32)
+        it = ctypes.c_int(0)
+        st = lib().rt_batch_lambda_iterate(self._h, ctypes.byref(atom.desc), descs, pp, max_iter,
+                                           float(tol), ctypes.byref(it),
+                                           hist.ctypes.data_as(L.PF), int(use_graph),
+                                           _stream(stream))
+        if st not in (L.RT_OK, L.RT_ENOCONV):
+            check(st)
+        return it.value, hist[:it.value].copy(), st == L.RT_OK

@@ -259,6 +259,27 @@ struct rt_batch {
     }
 };
 
+namespace rt {
+
+int batch_ngrids(const rt_batch *b) { return (int)b->grids.size(); }
+rt_grid *batch_grid(const rt_batch *b, int i) { return b->grids[i]; }
+int batch_nlam(const rt_batch *b) { return b->nlam; }
+
+rt_status batch_check_error(rt_batch *b, cudaStream_t st)
+{
+    unsigned h = 0;
+    RT_CUDA(cudaMemcpyAsync(&h, b->err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    RT_CUDA(cudaStreamSynchronize(st));
+    if (h) {
+        RT_CUDA(cudaMemsetAsync(b->err, 0, sizeof(unsigned), st));
+        if (h & ERR_NAN) return fail(RT_ENAN, "a non-finite value was produced on the device");
+        return fail(RT_EINVAL, "a device-side check failed in the batched sweep");
+    }
+    return RT_OK;
+}
+
+}  // namespace rt
+
 extern "C" {
 
 rt_status rt_batch_create(const rt_grid_t *grids, int ngrids, int nlam, const int *lam_chunk,

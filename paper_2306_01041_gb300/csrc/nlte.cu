@@ -1058,6 +1058,106 @@ rt_status rt_lambda_iterate_ex(rt_grid_t g, const rt_atom *atom, const rt_atmos 
     });
 }
 
+// The Lambda iteration of every atmosphere of a batch at once: per atmosphere the source terms,
+// then one batched formal solution of all of them, then per atmosphere the statistical
+// equilibrium, all writing one shared convergence scalar (the largest change over every
+// atmosphere).  One model atom serves the whole batch (its constants live in constant memory).
+rt_status rt_batch_lambda_iterate(rt_batch_t b, const rt_atom *atom, const rt_atmos *atms,
+                                  float *const *pops, int max_iter, double tol, int *iters_out,
+                                  float *history, int use_graph, void *stream)
+{
+    return guarded([&]() -> rt_status {
+        if (!b || !atms || !pops) return fail(RT_EINVAL, "null argument");
+        if (max_iter < 1) return fail(RT_EINVAL, "max_iter must be >= 1");
+        const int ng = batch_ngrids(b);
+        const int nlam = batch_nlam(b);
+        if (!atom || atom->nlam != nlam)
+            return fail(RT_EINVAL, "the atom's wavelength count must equal the batch's");
+        for (int i = 0; i < ng; ++i) RT_TRY(check_atmos(batch_grid(b, i), &atms[i], pops[i]));
+        RT_TRY(load_atom(atom));
+        cudaStream_t st = (cudaStream_t)stream;
+        // per atmosphere: alpha, S, J [nlam][n] in the grid's iteration scratch; the convergence
+        // scalar in the first grid's
+        std::vector<float *> A(ng), S(ng), J(ng);
+        float *dmax = nullptr;
+        for (int i = 0; i < ng; ++i) {
+            rt_grid *g = batch_grid(b, i);
+            const size_t m = (size_t)nlam * g->npt;
+            void *p;
+            RT_TRY(scratch_get(g, 2, 3 * m * sizeof(float) + 256, &p));
+            A[i] = (float *)p;
+            S[i] = A[i] + m;
+            J[i] = S[i] + m;
+            if (i == 0) dmax = (float *)((((uintptr_t)(J[i] + m)) + 15) & ~(uintptr_t)15);
+        }
+        float *h_dmax = nullptr;
+        RT_CUDA(cudaMallocHost(&h_dmax, sizeof(float)));
+        struct Guard {
+            float *h;
+            cudaGraphExec_t ex = nullptr;
+            cudaGraph_t gr = nullptr;
+            cudaStream_t cs = nullptr;
+            ~Guard()
+            {
+                if (ex) cudaGraphExecDestroy(ex);
+                if (gr) cudaGraphDestroy(gr);
+                if (cs) cudaStreamDestroy(cs);
+                cudaFreeHost(h);
+            }
+        } guard{h_dmax};
+        auto enqueue = [&](cudaStream_t s) -> rt_status {
+            RT_CUDA(cudaMemsetAsync(dmax, 0, sizeof(float), s));
+            for (int i = 0; i < ng; ++i) {
+                rt_grid *g = batch_grid(b, i);
+                const int64_t n = g->npt;
+                note_launch();
+                source_terms_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(
+                    n, atms[i].T, atms[i].rho, atms[i].ne, pops[i], A[i], S[i], g->d_err);
+            }
+            RT_TRY(rt_batch_formal_solution(b, A.data(), S.data(), RT_BC_THERMAL, J.data(), s));
+            for (int i = 0; i < ng; ++i) {
+                rt_grid *g = batch_grid(b, i);
+                const int64_t n = g->npt;
+                note_launch();
+                se_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+                    n, atms[i].T, atms[i].ne, atms[i].nH, J[i], pops[i], dmax, g->d_err);
+            }
+            RT_CUDA(cudaMemcpyAsync(h_dmax, dmax, sizeof(float), cudaMemcpyDeviceToHost, s));
+            return RT_OK;
+        };
+        if (use_graph) {
+            RT_CUDA(cudaStreamCreateWithFlags(&guard.cs, cudaStreamNonBlocking));
+            RT_CUDA(cudaStreamBeginCapture(guard.cs, cudaStreamCaptureModeThreadLocal));
+            rt_status s = enqueue(guard.cs);
+            cudaError_t e = cudaStreamEndCapture(guard.cs, &guard.gr);
+            if (s != RT_OK) {
+                cudaGetLastError();
+                return s;
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+            RT_CUDA(cudaGraphInstantiate(&guard.ex, guard.gr, 0));
+        }
+        int it = 0;
+        rt_status result = RT_ENOCONV;
+        for (it = 1; it <= max_iter; ++it) {
+            if (use_graph) RT_CUDA(cudaGraphLaunch(guard.ex, st));
+            else RT_TRY(enqueue(st));
+            RT_CUDA(cudaStreamSynchronize(st));
+            for (int i = 0; i < ng; ++i) RT_TRY(check_dev_error(batch_grid(b, i), st));
+            RT_TRY(batch_check_error(b, st));
+            const float d = *h_dmax;
+            if (history) history[it - 1] = d;
+            if (d < tol) {
+                result = RT_OK;
+                break;
+            }
+        }
+        if (iters_out) *iters_out = std::min(it, max_iter);
+        if (result == RT_ENOCONV) fail(RT_ENOCONV, "max_iter reached before the tolerance");
+        return result;
+    });
+}
+
 // Host evaluation of the device Voigt function for testing: H(a, v) in FP32 arithmetic is not
 // reproduced here; this returns G(v) = 2 v F(v) - 1 from the double-precision Dawson series that
 // seeds the device tables.

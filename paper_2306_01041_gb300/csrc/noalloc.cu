@@ -8,7 +8,6 @@
 // and its per-plane stencils as kernel arguments, so it needs no grid object and no device
 // allocation at all.  The caller passes the inputs and the output.
 #include <cmath>
-#include <mutex>
 #include <vector>
 
 #include "device_common.cuh"
@@ -92,23 +91,17 @@ __global__ void __launch_bounds__(256) sc_plane_noalloc_kernel(const NoAllocPlan
     *Jp = a.first ? jacc : *Jp + jacc;
 }
 
-// Device address of the static scratch, looked up once per device with that device current.
-static std::mutex g_noalloc_mu;
-static float *g_noalloc_ptr[64] = {nullptr};
-
+// Device address of the static scratch in the context current on the calling thread.  The
+// address belongs to a CUDA context, not to a device ordinal: a host application may run its own
+// driver context, and cudaDeviceReset replaces the primary one.  So it is looked up on every call,
+// which allocates nothing (the first lookup in a context may load the library's device code and
+// reserve the array there).
 static rt_status noalloc_scratch(float **out)
 {
-    int dev = 0;
-    RT_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return fail(RT_EINVAL, "device ordinal out of range");
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
-        g_noalloc_ptr[dev] = (float *)p;
-    }
-    *out = g_noalloc_ptr[dev];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
+    *out = (float *)p;
     return RT_OK;
 }
 

@@ -213,4 +213,10 @@ rt_status voronoi_build_tables(const rt_grid *g, int ndir, const double *dirs, V
 // tables of one extra direction, cached on the grid
 rt_status voronoi_dir_tables_cached(rt_grid *g, const double *dir, VorTables **out,
                                     cudaStream_t st);
+// a batch's grids and wavelength count (batch.cu), and its device error word: read, reset and
+// turned into a status (synchronises on st)
+int batch_ngrids(const rt_batch *b);
+rt_grid *batch_grid(const rt_batch *b, int i);
+int batch_nlam(const rt_batch *b);
+rt_status batch_check_error(rt_batch *b, cudaStream_t st);
 }  // namespace rt

@@ -28,10 +28,13 @@ from scipy.spatial import Delaunay
 from .atmosphere import Atmosphere
 
 
-def rejection_sample(f, n, lo, hi, seed, fmax, batch=1 << 18):
+def rejection_sample(f, n, lo, hi, seed, fmax, batch=1 << 18, f_upper=None):
     """``n`` sites in the box [lo, hi) (3-vectors) with density proportional to f(x, y, z).
 
-    ``fmax`` is the normalisation of the target density (its maximum over the box).
+    ``fmax`` is the normalisation of the target density (its maximum over the box).  ``f_upper``
+    (optional, a function of z alone with f_upper(z) >= f(x, y, z) everywhere) only saves work:
+    a proposal whose level already exceeds f_upper / fmax is rejected without evaluating f, which
+    takes the same decision.
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     lo = np.asarray(lo, float)
@@ -40,9 +43,14 @@ def rejection_sample(f, n, lo, hi, seed, fmax, batch=1 << 18):
     have = 0
     while have < n:
         p = lo + (hi - lo) * rng.random((batch, 3))
-        dens = f(p[:, 0], p[:, 1], p[:, 2]) / fmax
         rej = rng.random(batch)
-        acc = p[dens >= rej]
+        if f_upper is None:
+            keep = f(p[:, 0], p[:, 1], p[:, 2]) / fmax >= rej
+        else:
+            keep = f_upper(p[:, 2]) / fmax >= rej
+            c = np.nonzero(keep)[0]
+            keep[c] = f(p[c, 0], p[c, 1], p[c, 2]) / fmax >= rej[c]
+        acc = p[keep]
         out.append(acc)
         have += len(acc)
     return np.concatenate(out)[:n]
@@ -83,33 +91,38 @@ def _local_spacing(z, z0, z1, nbin=60):
 def delaunay_neighbours(xyz, box, periodic_xy=True, grow=4.5):
     """Neighbour CSR (off int64[N+1], code int32[M], shift int8[M]) of sites ``xyz`` [N, 3].
 
-    ``box`` = (x0, x1, y0, y1, z0, z1).  Images and mirror ghosts are generated within a
-    height-dependent margin (``grow`` times the local site spacing), grown until certified.
+    ``box`` = (x0, x1, y0, y1, z0, z1).  Periodic images and wall mirrors are generated within a
+    height-dependent margin (``grow`` times the local site spacing at the point's height, and for
+    the mirrors at least the gap between the wall and its nearest site), grown until certified:
+    every Delaunay tetrahedron touching a real site must have its circumsphere inside the region
+    where no image or mirror is missing.  The margin grows only in the height bins that a failing
+    circumsphere spans.
     """
     xyz = np.ascontiguousarray(xyz, dtype=np.float64)
     n = len(xyz)
     x0, x1, y0, y1, z0, z1 = box
     Lx, Ly, Lz = x1 - x0, y1 - y0, z1 - z0
     edges, cnt = _local_spacing(xyz[:, 2], z0, z1)
-    bin_vol = Lx * Ly * (edges[1] - edges[0])
+    hb = edges[1] - edges[0]
+    nbin = len(edges) - 1
+    bin_vol = Lx * Ly * hb
     spacing = (bin_vol / np.maximum(cnt, 0.5)) ** (1.0 / 3.0)
     zs = np.sort(xyz[:, 2])
-    k = min(64, n - 1)
-    # spacing among the sites nearest each wall, from the height span of the k nearest
-    s_bot = (Lx * Ly * max(zs[k] - zs[0], 1e-9 * Lz) / k) ** (1.0 / 3.0)
-    s_top = (Lx * Ly * max(zs[-1] - zs[-1 - k], 1e-9 * Lz) / k) ** (1.0 / 3.0)
     gap_bot = zs[0] - z0
     gap_top = z1 - zs[-1]
-    fac = grow
+
+    def bin_of(z):
+        return np.clip(((z - z0) / hb).astype(int), 0, nbin - 1)
+
+    fac = np.full(nbin, float(grow))
     while True:
-        m_bin = np.minimum(fac * spacing, max(Lx, Ly))
+        m_bin = np.minimum(fac * spacing, max(Lx, Ly, Lz))
         # a margin may only shrink slowly with height so that big cells above dense layers are
         # still covered: take the running maximum over a window of neighbouring bins
-        m_bin = np.maximum.reduce([np.roll(m_bin, k) for k in (-2, -1, 0, 1, 2)])
-        m_bot = gap_bot + fac * s_bot
-        m_top = gap_top + fac * s_top
-        b = np.clip(((xyz[:, 2] - z0) / (edges[1] - edges[0])).astype(int), 0, len(m_bin) - 1)
-        m_pt = m_bin[b]
+        # (the window does not wrap around: the sparse top must not widen the dense bottom's)
+        mp = np.pad(m_bin, 2, mode="edge")
+        m_bin = np.maximum.reduce([mp[k:k + nbin] for k in range(5)])
+        m_pt = m_bin[bin_of(xyz[:, 2])]
         pts = [xyz]
         orig = [np.arange(n)]
         sh = [np.full(n, 4, np.int8)]
@@ -127,9 +140,14 @@ def delaunay_neighbours(xyz, box, periodic_xy=True, grow=4.5):
         P = np.concatenate(pts)
         O = np.concatenate(orig)
         S = np.concatenate(sh)
+        mP = m_bin[bin_of(P[:, 2])]
         gp, go, gs = [P], [O.astype(np.int64)], [S]
-        for zw, tag, mw in ((z0, 1, m_bot), (z1, 2, m_top)):
-            keep = np.abs(P[:, 2] - zw) < mw
+        depth = {}
+        for zw, tag, gap in ((z0, 1, gap_bot), (z1, 2, gap_top)):
+            dist = np.abs(P[:, 2] - zw)
+            keep = dist < gap + mP
+            # the nearest missing mirror lies this far beyond the wall
+            depth[tag] = dist[~keep].min() if (~keep).any() else np.inf
             q = P[keep].copy()
             q[:, 2] = 2.0 * zw - q[:, 2]
             gp.append(q)
@@ -142,24 +160,26 @@ def delaunay_neighbours(xyz, box, periodic_xy=True, grow=4.5):
         simp = tri.simplices
         real_simp = (simp < n).any(axis=1)
         cen, r = _circumsphere(P, simp[real_simp])
-        # certified when each circumsphere stays inside the region where every image and ghost
-        # exists: above z0 - m_bot, below z1 + m_top, and horizontally within the smallest
-        # margin of the heights it spans
         fin = np.isfinite(r)
         cen, r = cen[fin], r[fin]
-        ok = (cen[:, 2] - r > z0 - m_bot) & (cen[:, 2] + r < z1 + m_top)
+        zl, zh = cen[:, 2] - r, cen[:, 2] + r
+        ok = (zl > z0 - depth[1]) & (zh < z1 + depth[2])
+        # images exist within the margin of their real site's height; a mirror beyond a wall
+        # stands for a point at the reflected height
+        lo = np.minimum(np.maximum(zl, z0), np.where(zh > z1, 2 * z1 - zh, np.inf))
+        hi = np.maximum(np.minimum(zh, z1), np.where(zl < z0, 2 * z0 - zl, -np.inf))
+        blo, bhi = bin_of(np.maximum(lo, z0)), bin_of(np.minimum(hi, z1))
         if periodic_xy:
-            zlo = np.clip(((cen[:, 2] - r - z0) / (edges[1] - edges[0])).astype(int), 0,
-                          len(m_bin) - 1)
-            zhi = np.clip(((cen[:, 2] + r - z0) / (edges[1] - edges[0])).astype(int), 0,
-                          len(m_bin) - 1)
-            mmin = _range_min(m_bin, zlo, zhi)
+            mmin = _range_min(m_bin, blo, bhi)
             ok &= ((cen[:, 0] - r > x0 - mmin) & (cen[:, 0] + r < x1 + mmin) &
                    (cen[:, 1] - r > y0 - mmin) & (cen[:, 1] + r < y1 + mmin))
         if ok.all():
             break
-        fac *= 1.5
-        if fac > 50.0:
+        grow_bin = np.zeros(nbin + 1, np.int64)
+        np.add.at(grow_bin, blo[~ok], 1)
+        np.add.at(grow_bin, bhi[~ok] + 1, -1)
+        fac[np.cumsum(grow_bin)[:nbin] > 0] *= 1.5
+        if fac.max() > 50.0:
             raise RuntimeError("Delaunay margin exceeded the box: too few sites")
     indptr, indices = tri.vertex_neighbor_vertices
     cnt_nb = np.diff(indptr[:n + 1])
@@ -205,6 +225,22 @@ def site_density(atm: Atmosphere, kind: str):
     raise ValueError(kind)
 
 
+def site_density_envelope(atm: Atmosphere, kind: str):
+    """A function of z alone bounding the target of ``site_density`` from above (None where the
+    target depends on z only).  For "dtau": |g| <= sum of the absolute Fourier coefficients, so
+    T <= T0(z) (1 + amp G), and the opacity grows with T; a relative margin of 1e-9 covers the
+    rounding of both evaluations."""
+    if kind != "dtau":
+        return None
+    f, cap = site_density(atm, kind)
+    G = float(np.abs(atm._ca).sum() + np.abs(atm._sa).sum())
+
+    def f_upper(z):
+        Tu = atm.T0(z) * (1.0 + atm.amp * G)
+        return np.minimum(atm.kappa0 * atm.rho(z) * (Tu / 5000.0) ** 9, cap) * (1.0 + 1e-9)
+    return f_upper
+
+
 def _cache_path(key):
     root = os.environ.get("RT_SYNTH_CACHE", os.path.join(os.path.expanduser("~"), ".cache",
                                                          "rt_synth"))
@@ -215,7 +251,7 @@ def _cache_path(key):
 def make_voronoi_grid(atm: Atmosphere, nsites: int, kind: str, seed: int, uniform_frac=0.0,
                       cache=True):
     """Sites plus neighbour CSR for the synthetic box of ``atm`` (cached on disk by key)."""
-    key = f"vor_a{atm.seed}_n{nsites}_{kind}_s{seed}_u{uniform_frac:g}_v1"
+    key = f"vor_a{atm.seed}_n{nsites}_{kind}_s{seed}_u{uniform_frac:g}_v2"
     if cache:
         path = _cache_path(key)
         if os.path.exists(path):
@@ -226,7 +262,8 @@ def make_voronoi_grid(atm: Atmosphere, nsites: int, kind: str, seed: int, unifor
     hi = (atm.Lx, atm.Ly, atm.zmax)
     n_uni = int(round(uniform_frac * nsites))
     f, fmax = site_density(atm, kind)
-    xyz = rejection_sample(f, nsites - n_uni, lo, hi, seed, fmax)
+    xyz = rejection_sample(f, nsites - n_uni, lo, hi, seed, fmax,
+                           f_upper=site_density_envelope(atm, kind))
     if n_uni:
         rng = np.random.Generator(np.random.PCG64(seed + 7919))
         xyz = np.concatenate([xyz, np.asarray(lo) + (np.asarray(hi) - np.asarray(lo)) *

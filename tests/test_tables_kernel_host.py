@@ -4,7 +4,7 @@ compiled for the host and run thread by thread, against the FP64 oracle (CPU onl
 The kernels compute every geometric step with explicit round-to-nearest double intrinsics; on
 the host those are the plain IEEE double operations (compiled without contraction), so the run
 performs the same arithmetic.  This checks the kernels' indexing, tie rules, wall handling and
-level relaxation on every CPU test run; the run on the GPU is test_zz_tables_device.py.
+level relaxation on every CPU test run; the run on the GPU is test_gpu_tables_device.py.
 """
 import os
 import shutil
