@@ -287,6 +287,18 @@ rt_status rt_emergent_intensity(rt_grid_t grid, const double dir[3], int nlam,
                                 const float *alpha, const float *S, int bc, float *I_top,
                                 void *stream);
 
+/* Emergent map (Sect. 2.5, last paragraph): the intensity along dir at the emergent layer, on an
+ * npx x npy pixel grid, map [nlam][npy][npx] (device, x fastest).  Regular grid: the top plane
+ * itself (npx = nx and npy = ny required; pixel (i, j) is grid point (i, j)).  Voronoi grid: the
+ * intensities at the sites of rt_grid_top_points, resampled to pixel (i, j) at
+ * (x0 + i Lx / npx, y0 + j Ly / npy) by inverse-distance weighting over the two nearest of those
+ * sites in (x, y) -- minimum image in the periodic x and y, ties to the smaller site index,
+ * weights 1/d normalised, (1, 0) on a site.  The pixel table is built on the host on the first
+ * call for an (npx, npy) and kept with the grid (allocates then).  bc as for
+ * rt_emergent_intensity. */
+rt_status rt_emergent_map(rt_grid_t grid, const double dir[3], int nlam, const float *alpha,
+                          const float *S, int bc, int npx, int npy, float *map, void *stream);
+
 /* Gradient of L = sum(gI_top * I_top) with respect to alpha and S at every point, for the
  * emergent intensity above: g_alpha, g_S [nlam][npt] device, overwritten.  The forward
  * intensities are kept only every ckpt_stride planes/levels (>= 1) and recomputed in between;

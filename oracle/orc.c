@@ -25,8 +25,10 @@
  * Linear-S integration over one optical-depth interval (Sect. 2.5: S linearly interpolated
  * across the interval; Eq. 2).  With d = delta tau, the source integral over the interval is
  *   int_0^d S(t) exp(-(d - t)) dt = w0 * S_up + w1 * S_here,
- *   e0 = 1 - exp(-d),  e1 = d - e0,  w1 = e1 / d,  w0 = e0 - w1.
- * Below d = 1e-6 the cancellation in e1 is avoided with the Taylor series of w0 and w1.
+ *   e0 = 1 - exp(-d),  e1 = d - e0,  w1 = e1 / d,  w0 = e0 - w1 = e0 / d - exp(-d).
+ * Below d = 1e-6 the cancellation in e1 is avoided with the Taylor series of w0 and w1; w0 is
+ * evaluated as e0 / d - exp(-d), which keeps its relative precision for very thick intervals
+ * (there w0 -> 1/d while w1 -> 1, and e0 - w1 would cancel).
  * ------------------------------------------------------------------------------------- */
 void orc_linear_weights(double d, double *ex, double *w0, double *w1)
 {
@@ -39,7 +41,7 @@ void orc_linear_weights(double d, double *ex, double *w0, double *w1)
     double e0 = -expm1(-d);
     *ex = exp(-d);
     *w1 = (d - e0) / d;
-    *w0 = e0 - *w1;
+    *w0 = e0 / d - *ex;
 }
 
 /* derivatives of (exp(-d), w0, w1) with respect to d, for the adjoint */

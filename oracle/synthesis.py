@@ -97,3 +97,27 @@ def final_synthesis(atom, site_pops, sites, box, mesh, mesh_fields):
     pops = interpolate(site_pops, k, idw_weights(d))
     alpha, S = atom.alpha_S(mesh_fields["T"], mesh_fields["rho"], mesh_fields["ne"], pops)
     return emergent_mu1(nx, ny, nz, dx, dy, z, alpha, S)
+
+
+def top_sites(nbr_off, nbr_idx):
+    """Sites of the emergent layer: those whose neighbour list holds a mirror in the top wall
+    (neighbour code -2 - 2k), in increasing site order."""
+    off = np.asarray(nbr_off)
+    code = np.asarray(nbr_idx)
+    row = np.repeat(np.arange(len(off) - 1), np.diff(off))
+    top_mirror = (code < 0) & (((-code - 1) & 1) == 1)
+    return np.unique(row[top_mirror])
+
+
+def resample_map(sites_xy, values, npx, npy, box):
+    """Emergent intensities at the top sites ([nf][ntop], positions [ntop][2]) on an npx x npy
+    pixel grid [nf][npy npx]: pixel (i, j) at (x0 + i Lx / npx, y0 + j Ly / npy), two nearest
+    sites in (x, y) with the minimum image in x and y (brute force, ties to the smaller index),
+    weights 1/d normalised, (1, 0) on a site."""
+    Lx, Ly = box[1] - box[0], box[3] - box[2]
+    J, I = np.meshgrid(np.arange(npy), np.arange(npx), indexing="ij")
+    px = np.stack([box[0] + I.ravel() * Lx / npx, box[2] + J.ravel() * Ly / npy,
+                   np.zeros(npx * npy)], axis=1)
+    sites = np.column_stack([np.asarray(sites_xy, float)[:, :2], np.zeros(len(sites_xy))])
+    k, d = two_nearest_bruteforce(sites, px, box)
+    return interpolate(values, k, idw_weights(d))

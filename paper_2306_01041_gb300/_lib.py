@@ -92,6 +92,7 @@ SIGNATURES = {
     "rt_idw_table": (c_int, [P, PI32, PF]),
     "rt_idw_interpolate": (c_int, [P, c_int, P, P, P]),
     "rt_emergent_intensity": (c_int, [P, PD, c_int, P, P, c_int, P, P]),
+    "rt_emergent_map": (c_int, [P, PD, c_int, P, P, c_int, c_int, c_int, P, P]),
     "rt_adjoint_workspace_size": (c_size_t, [P, c_int, c_int]),
     "rt_formal_solution_adjoint": (c_int, [P, PD, c_int, P, P, c_int, P, P, P, c_int, P, c_size_t,
                                            P]),

@@ -414,6 +414,19 @@ def emergent_intensity(grid, direction, alpha, S, bc=L.RT_BC_THERMAL, stream=Non
     return out
 
 
+def emergent_map(grid, direction, alpha, S, npx, npy, bc=L.RT_BC_THERMAL, stream=None):
+    """Emergent intensity along one direction on an npx x npy pixel grid, [nlam][npy * npx]:
+    the top plane of a regular grid, or the emergent-layer sites of a Voronoi grid resampled by
+    two-nearest inverse-distance weighting in (x, y)."""
+    nlam = alpha.shape[0]
+    d = (ctypes.c_double * 3)(*[float(v) for v in direction])
+    out = torch.empty((nlam, npy * npx), device=alpha.device, dtype=torch.float32)
+    check(lib().rt_emergent_map(grid.handle, d, nlam, _dev(alpha, (nlam, grid.npt), "alpha"),
+                                _dev(S, (nlam, grid.npt), "S"), bc, int(npx), int(npy), _dev(out),
+                                _stream(stream)))
+    return out
+
+
 def formal_solution_adjoint(grid, direction, alpha, S, gI_top, bc=L.RT_BC_THERMAL,
                             ckpt_stride=1, stream=None):
     nlam = alpha.shape[0]

@@ -435,6 +435,7 @@ rt_grid::~rt_grid()
     if (d_stencil_oned) cudaFree(d_stencil_oned);
     if (d_wave_st) cudaFree(d_wave_st);
     face_release(face);
+    map_release(map);
     if (d_up_site) cudaFree(d_up_site);
     if (self_batch) rt_batch_destroy(self_batch);
     vt.release();

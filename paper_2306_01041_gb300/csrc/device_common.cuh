@@ -23,11 +23,13 @@ __device__ __forceinline__ float rcp_fast(float x)
 }
 
 // Linear-S integration over one optical-depth interval d (Sect. 2.5: S linear across the
-// interval; Eq. 2):  I = I_up e^-d + w0 S_up + w1 S with e0 = 1 - e^-d, w1 = (d - e0) / d,
-// w0 = e0 - w1.  Below d = 0.1 both weights come from their Taylor series (truncated after d^5,
-// relative error < 3e-8): in optically thin layers I can be far below S, so the weights need
-// relative, not just absolute, accuracy.  Above, w1 = 1 - e0 / d with the fast reciprocal
-// (e0 >= 0.095 there, so e0 = 1 - e^-d keeps full relative precision).
+// interval; Eq. 2):  I = I_up e^-d + w0 S_up + w1 S with e0 = 1 - e^-d, w1 = 1 - e0 / d,
+// w0 = e0 / d - e^-d (= e0 - w1).  Below d = 0.1 both weights come from their Taylor series
+// (truncated after d^5, relative error < 3e-8): in optically thin layers I can be far below S, so
+// the weights need relative, not just absolute, accuracy.  Above, both are single fused
+// multiply-adds on e0 / d (fast reciprocal; e0 >= 0.095 there keeps full relative precision).
+// w0 is not taken as e0 - w1: for d beyond ~1e7 w1 rounds to 1 in FP32 and the difference would
+// lose w0 ~ 1/d entirely, while w0 S_up still matters where S_up exceeds S by a factor near d.
 __device__ __forceinline__ void lin_weights(float d, float &ex, float &w0, float &w1)
 {
     ex = exp_neg(d);
@@ -38,8 +40,9 @@ __device__ __forceinline__ void lin_weights(float d, float &ex, float &w0, float
                                                 d * (-1.0f / 30.0f + d * (1.0f / 144.0f)))));
     } else {
         const float e0 = 1.0f - ex;
-        w1 = 1.0f - e0 * rcp_fast(d);
-        w0 = e0 - w1;
+        const float r = rcp_fast(d);
+        w1 = fmaf(-e0, r, 1.0f);
+        w0 = fmaf(e0, r, -ex);
     }
 }
 
@@ -53,7 +56,7 @@ __device__ __forceinline__ void lin_weights(double d, double &ex, double &w0, do
     } else {
         const double e0 = -expm1(-d);
         w1 = (d - e0) / d;
-        w0 = e0 - w1;
+        w0 = e0 / d - ex;
     }
 }
 

@@ -141,6 +141,94 @@ void two_nearest(const rt_grid *v, const Bins &b, const double q[3], Near &n1, N
 }
 
 }  // namespace
+
+// Pixel table of the emergent map on a Voronoi grid: the two nearest emergent-layer sites of every
+// pixel in (x, y), with their weights, and a buffer for the intensities at those sites.
+struct MapTable {
+    int npx = 0, npy = 0;
+    int64_t ntop = 0;
+    int2 *d_k = nullptr;      // [npy * npx] positions in the grid's top list
+    float2 *d_w = nullptr;
+    float *d_itop = nullptr;  // [nlam][ntop]
+    int itop_nlam = 0;
+};
+
+void map_release(MapTable *t)
+{
+    if (!t) return;
+    cudaFree(t->d_k);
+    cudaFree(t->d_w);
+    cudaFree(t->d_itop);
+    delete t;
+}
+
+// Builds (or reuses) the pixel table of an npx x npy map: pixel (i, j) at (x0 + i Lx / npx,
+// y0 + j Ly / npy); two nearest top sites by distance in (x, y) with the minimum image in the
+// periodic x and y, ties to the earlier site of the top list (the smaller site index); weights
+// 1/d normalised, (1, 0) on a site.
+static rt_status map_table(rt_grid *g, int npx, int npy, int nlam, MapTable **out)
+{
+    MapTable *t = g->map;
+    if (!t || t->npx != npx || t->npy != npy) {
+        map_release(t);
+        g->map = nullptr;
+        t = new MapTable();
+        t->npx = npx;
+        t->npy = npy;
+        t->ntop = (int64_t)g->top.size();
+        const double Lx = g->box[1] - g->box[0], Ly = g->box[3] - g->box[2];
+        const int64_t np = (int64_t)npx * npy;
+        std::vector<int2> hk(np);
+        std::vector<float2> hw(np);
+    #pragma omp parallel for schedule(static)
+        for (int64_t p = 0; p < np; ++p) {
+            const double qx = g->box[0] + (double)(p % npx) * Lx / npx;
+            const double qy = g->box[2] + (double)(p / npx) * Ly / npy;
+            double d1 = INFINITY, d2 = INFINITY;
+            int k1 = -1, k2 = -1;
+            for (int64_t q = 0; q < t->ntop; ++q) {
+                const double *s = &g->xyz[3 * (size_t)g->top[q]];
+                double ex = s[0] - qx, ey = s[1] - qy;
+                ex -= Lx * std::nearbyint(ex / Lx);
+                ey -= Ly * std::nearbyint(ey / Ly);
+                const double d = ex * ex + ey * ey;
+                if (d < d1) {
+                    d2 = d1;
+                    k2 = k1;
+                    d1 = d;
+                    k1 = (int)q;
+                } else if (d < d2) {
+                    d2 = d;
+                    k2 = (int)q;
+                }
+            }
+            float w1 = 1.f, w2 = 0.f;
+            if (d1 > 0.0) {
+                const double a = 1.0 / std::sqrt(d1), c = 1.0 / std::sqrt(d2);
+                w1 = (float)(a / (a + c));
+                w2 = (float)(c / (a + c));
+            }
+            hk[p] = make_int2(k1, k2);
+            hw[p] = make_float2(w1, w2);
+        }
+        cudaError_t e = cudaMalloc(&t->d_k, np * sizeof(int2));
+        if (e == cudaSuccess) e = cudaMalloc(&t->d_w, np * sizeof(float2));
+        if (e == cudaSuccess) e = cudaMemcpy(t->d_k, hk.data(), np * sizeof(int2), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(t->d_w, hw.data(), np * sizeof(float2), cudaMemcpyHostToDevice);
+        g->map = t;
+        if (e != cudaSuccess) return cuda_fail(e, "emergent map table upload");
+    }
+    if (t->itop_nlam < nlam) {
+        cudaFree(t->d_itop);
+        t->d_itop = nullptr;
+        t->itop_nlam = 0;
+        RT_CUDA(cudaMalloc(&t->d_itop, (size_t)nlam * std::max<int64_t>(1, t->ntop) * sizeof(float)));
+        t->itop_nlam = nlam;
+    }
+    *out = t;
+    return RT_OK;
+}
+
 }  // namespace rt
 
 using namespace rt;
@@ -219,6 +307,30 @@ rt_status rt_idw_interpolate(rt_idw_t t, int nf, const float *src, float *dst, v
         note_launch();
         idw_gather_kernel<<<(unsigned)((work + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
             t->d_k, t->d_w, src, dst, t->npt, t->nsites, nf);
+        RT_CUDA(cudaGetLastError());
+        return RT_OK;
+    });
+}
+
+rt_status rt_emergent_map(rt_grid_t g, const double dir[3], int nlam, const float *alpha,
+                          const float *S, int bc, int npx, int npy, float *map, void *stream)
+{
+    return guarded([&]() -> rt_status {
+        if (!g || !dir || !alpha || !S || !map) return fail(RT_EINVAL, "null argument");
+        if (nlam < 1 || npx < 1 || npy < 1) return fail(RT_EINVAL, "nlam, npx and npy must be >= 1");
+        if (g->kind == RT_GRID_REGULAR) {
+            if (npx != g->nx || npy != g->ny)
+                return fail(RT_EINVAL, "on a regular grid the map is the top plane: npx = nx, npy = ny");
+            return rt_emergent_intensity(g, dir, nlam, alpha, S, bc, map, stream);
+        }
+        if (g->top.size() < 2) return fail(RT_EINVAL, "need at least two emergent-layer sites");
+        MapTable *t = nullptr;
+        RT_TRY(map_table(g, npx, npy, nlam, &t));
+        RT_TRY(rt_emergent_intensity(g, dir, nlam, alpha, S, bc, t->d_itop, stream));
+        const int64_t np = (int64_t)npx * npy, work = np * nlam;
+        note_launch();
+        idw_gather_kernel<<<(unsigned)((work + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+            t->d_k, t->d_w, t->d_itop, map, np, t->ntop, nlam);
         RT_CUDA(cudaGetLastError());
         return RT_OK;
     });

@@ -89,8 +89,9 @@ __device__ __forceinline__ void lin_weights_thick(float d, float &ex, float &w0,
 {
     ex = exp_neg(d);
     const float e0 = 1.0f - ex;
-    w1 = 1.0f - e0 * rcp_fast(d);
-    w0 = e0 - w1;
+    const float r = rcp_fast(d);
+    w1 = fmaf(-e0, r, 1.0f);
+    w0 = fmaf(e0, r, -ex);
 }
 
 // Per-point updates of one staged item for every direction.  THICK: every interval of the item

@@ -103,6 +103,8 @@ struct VorTables {
 
 struct FaceTables;                             // face-hitting scheme tables (regular_face.cu)
 void face_release(FaceTables *t);
+struct MapTable;                               // emergent map's pixel table (idw.cu)
+void map_release(MapTable *t);
 
 struct Scratch {
     void *p = nullptr;
@@ -151,6 +153,7 @@ struct rt_grid {
     int max_levels = 0;
     std::vector<int64_t> top;                  // emergent-layer points
     int64_t *d_top = nullptr;
+    rt::MapTable *map = nullptr;               // cache: pixel table of rt_emergent_map
     // shared
     unsigned *d_err = nullptr;                 // device error word
     rt::Scratch scratch[5];

@@ -138,8 +138,14 @@ def regular_axes(nx: int, ny: int, nz: int, atm: Atmosphere):
 
 
 def regular_fields(nx: int, ny: int, nz: int, atm: Atmosphere):
-    """Fields on the regular grid, flattened with x fastest: index = (k * ny + j) * nx + i."""
+    """Fields on the regular grid, flattened with x fastest: index = (k * ny + j) * nx + i.
+    The horizontal field g is evaluated once per column (it does not depend on z)."""
     x, y, z, dx, dy = regular_axes(nx, ny, nz, atm)
-    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
-    f = atm.fields(X, Y, Z)
-    return {k: v.reshape(-1) for k, v in f.items()}, (x, y, z, dx, dy)
+    Y2, X2 = np.meshgrid(y, x, indexing="ij")
+    g = atm.g(X2.ravel(), Y2.ravel()).reshape(ny, nx)
+    T = atm.T0(z)[:, None, None] * (1.0 + atm.amp * g)[None]
+    rho = np.broadcast_to(atm.rho(z)[:, None, None], (nz, ny, nx))
+    nH = rho / (1.4 * M_H)
+    ne = atm.n_e(T, nH)
+    f = dict(T=T, rho=rho, ne=ne, nH=nH)
+    return {k: np.ascontiguousarray(v).reshape(-1) for k, v in f.items()}, (x, y, z, dx, dy)

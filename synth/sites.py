@@ -115,6 +115,12 @@ def delaunay_neighbours(xyz, box, periodic_xy=True, grow=4.5):
         return np.clip(((z - z0) / hb).astype(int), 0, nbin - 1)
 
     fac = np.full(nbin, float(grow))
+    # the sparsest height bins, holding together at most 0.5 % of the sites, are replicated in
+    # full from the start: their big cells would fail the certification of any local margin, and
+    # replicating them costs little
+    raw, _ = np.histogram(xyz[:, 2], bins=edges)
+    by_count = np.argsort(raw, kind="stable")
+    fac[by_count[np.cumsum(raw[by_count]) <= 0.005 * n]] = np.inf
     while True:
         m_bin = np.minimum(fac * spacing, max(Lx, Ly, Lz))
         # a margin may only shrink slowly with height so that big cells above dense layers are
@@ -179,7 +185,7 @@ def delaunay_neighbours(xyz, box, periodic_xy=True, grow=4.5):
         np.add.at(grow_bin, blo[~ok], 1)
         np.add.at(grow_bin, bhi[~ok] + 1, -1)
         fac[np.cumsum(grow_bin)[:nbin] > 0] *= 1.5
-        if fac.max() > 50.0:
+        if fac[np.isfinite(fac)].max(initial=0.0) > 50.0:
             raise RuntimeError("Delaunay margin exceeded the box: too few sites")
     indptr, indices = tri.vertex_neighbor_vertices
     cnt_nb = np.diff(indptr[:n + 1])

@@ -90,3 +90,108 @@ def test_autotuner_choice_is_correct_and_cached(rt, tmp_path, monkeypatch):
                       rel=1e-6, what="tuned batch")
     _, again = at.tune_batch(grids, alphas, Ss, nlam)
     assert again == choice
+
+
+# ---- the batch against the FP64 oracle ---------------------------------------------------------
+def _atm_grid(rt, n, kind, seed, atm_seed):
+    from helpers import voronoi_grid
+    atm, vg, f = voronoi_grid(n, kind, seed, atm_seed)
+    dirs, w = s4_quadrature()
+    G = rt.VoronoiGrid(vg["xyz"], vg["nbr_off"], vg["nbr_idx"], vg["nbr_shift"], vg["box"], dirs,
+                       w)
+    return atm, vg, f, G
+
+
+def _lte_fields(atm, f, data):
+    """alpha, S [52][n] of the NLTE atom at its LTE populations (FP64, the oracle's physics)."""
+    from oracle.physics import Atom
+    A = Atom(data, atm.kappa0)
+    pops = A.lte_pops(f["T"], f["ne"], f["nH"])
+    return A.alpha_S(f["T"], f["rho"], f["ne"], pops)
+
+
+@pytest.mark.parametrize("lam_chunk", [None, [4, 13, 52]])
+def test_batch_uneven_grids_match_oracle(rt, lam_chunk):
+    """Three atmosphere grids of uneven size (1500, 4000, 9000 sites; rho^0.3 and |dtau/dz|
+    sampling), the 52 wavelengths of the atom and 24 directions in one batched launch, with the
+    built-in wavelength chunks and with chunks of 4, 13 and 52: J of every grid against the
+    oracle's level sweep (Sect. 2.5, Eq. 5)."""
+    import oracle
+    from synth import model_atom
+    specs = [(1500, "rho03", 21), (4000, "dtau", 22), (9000, "rho03", 23)]
+    grids, fields, vgs = [], [], []
+    for n, kind, seed in specs:
+        atm, vg, f, G = _atm_grid(rt, n, kind, seed, 0)
+        data = model_atom(np.min(f["ne"] / np.sqrt(f["T"])))
+        fields.append(_lte_fields(atm, f, data))
+        grids.append(G)
+        vgs.append(vg)
+    batch = rt.Batch(grids, 52, lam_chunk=lam_chunk)
+    Jb = batch.formal_solution([to_gpu(a) for a, s in fields], [to_gpu(s) for a, s in fields])
+    dirs, w = s4_quadrature()
+    for vg, (a, s), jb in zip(vgs, fields, Jb):
+        tab = oracle.voronoi_tables(vg["xyz"], vg["nbr_off"], vg["nbr_idx"], vg["nbr_shift"],
+                                    vg["box"], dirs, 7.0)
+        assert_parity(jb.cpu().numpy(), oracle.voronoi_fs(tab, dirs, w, a, s), what="batched J")
+
+
+def test_batch_with_a_deep_grid_matches_oracle(rt):
+    """The 160 000-site rho^0.3 atmosphere of the 8-atmosphere workload (more than 100 dependency
+    levels in its deepest directions) batched with a 20 000-site |dtau/dz| grid, 52 wavelengths:
+    J at a line-core, a line-wing and a continuum wavelength against the oracle, at every site."""
+    import oracle
+    from synth import model_atom
+    dirs, w = s4_quadrature()
+    specs = [(160000, "rho03", 5, 5), (20000, "dtau", 10, 0)]
+    grids, fields, vgs = [], [], []
+    for n, kind, seed, atm_seed in specs:
+        atm, vg, f, G = _atm_grid(rt, n, kind, seed, atm_seed)
+        data = model_atom(np.min(f["ne"] / np.sqrt(f["T"])))
+        fields.append(_lte_fields(atm, f, data))
+        grids.append(G)
+        vgs.append(vg)
+    assert grids[0].max_levels > 100
+    batch = rt.Batch(grids, 52)
+    Jb = batch.formal_solution([to_gpu(a) for a, s in fields], [to_gpu(s) for a, s in fields])
+    pick = [25, 40, 50]
+    for vg, (a, s), jb in zip(vgs, fields, Jb):
+        tab = oracle.voronoi_tables(vg["xyz"], vg["nbr_off"], vg["nbr_idx"], vg["nbr_shift"],
+                                    vg["box"], dirs, 7.0)
+        ref = oracle.voronoi_fs(tab, dirs, w, a[pick], s[pick])
+        assert_parity(jb.cpu().numpy()[pick], ref, what="deep-grid batched J")
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_batched_lambda_iteration_matches_oracle(rt, use_graph):
+    """Three Lambda iterations (Sect. 2.1, Eq. 3-4) of two atmospheres' grids together
+    (rt_batch_lambda_iterate, one CUDA graph per iteration or eager launches) against the
+    oracle's iteration of each grid on its own: populations after every grid's third update."""
+    from oracle.physics import Atom
+    from oracle.solve import VoronoiGrid as OrcVoronoi
+    from oracle.solve import lambda_iterate as orc_lambda_iterate
+    from synth import model_atom
+    dirs, w = s4_quadrature()
+    specs = [(2000, "rho03", 31), (3500, "dtau", 32)]
+    grids, fs, vgs = [], [], []
+    for n, kind, seed in specs:
+        atm, vg, f, G = _atm_grid(rt, n, kind, seed, 0)
+        grids.append(G)
+        fs.append(f)
+        vgs.append(vg)
+    data = model_atom(min(np.min(f["ne"] / np.sqrt(f["T"])) for f in fs))
+    A = Atom(data, atm.kappa0)
+    ga = rt.Atom(data, atm.kappa0)
+    atms = [rt.Atmos(to_gpu(f["T"]), to_gpu(f["rho"]), to_gpu(f["ne"]), to_gpu(f["nH"]))
+            for f in fs]
+    pops = [rt.lte_populations(G, ga, M) for G, M in zip(grids, atms)]
+    batch = rt.Batch(grids, len(data["lam"]))
+    its, hist, conv = batch.lambda_iterate(ga, atms, pops, max_iter=3, tol=0.0,
+                                           use_graph=use_graph)
+    assert its == 3 and not conv
+    hmax = np.zeros(3)
+    for vg, f, p in zip(vgs, fs, pops):
+        ref, it, h = orc_lambda_iterate(OrcVoronoi(vg, dirs, w), A, f["T"], f["rho"], f["ne"],
+                                        f["nH"], max_iter=3, tol=0.0)
+        assert_parity(p.cpu().numpy(), ref, rel=1e-4, floor=0.0, what="batched iteration pops")
+        hmax = np.maximum(hmax, h)
+    np.testing.assert_allclose(hist, hmax, rtol=2e-2)

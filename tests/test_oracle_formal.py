@@ -36,6 +36,18 @@ def test_linear_weights_match_quadrature(d):
     assert dex == pytest.approx(-math.exp(-d), rel=1e-14)
 
 
+@pytest.mark.parametrize("d", [50.0, 1e3, 1e6, 1e9, 1e13])
+def test_linear_weights_thick_closed_form(d):
+    """Optically thick intervals: the hat-function integrals have the closed forms
+    w0 = (1 - (1 + d) e^-d) / d and w1 = (1 - e^-d) - w0, so w0 -> 1/d while w1 -> 1.  w0 keeps
+    full relative precision however thick the interval (it carries the upwind source function,
+    which can exceed the local one by a factor comparable to d)."""
+    (ex, w0, w1), _ = oracle.linear_weights(d)
+    ref0 = -math.expm1(-d) / d - (1.0 + 1.0 / d) * math.exp(-d) if d < 700 else 1.0 / d
+    assert w0 == pytest.approx(ref0, rel=1e-13)
+    assert w1 == pytest.approx(-math.expm1(-d) - ref0, rel=1e-15)
+
+
 def _grid_z(nz, nonuniform=True, L=1.0, seed=3):
     rng = np.random.default_rng(seed)
     dz = np.ones(nz - 1) if not nonuniform else 0.5 + rng.random(nz - 1)
