@@ -1,14 +1,22 @@
-"""Benchmark: one Lambda iteration of the NLTE problem on the 128^3 regular grid.
+"""Benchmark: one Lambda iteration of the NLTE problem on the 128^3 regular grid, plus the
+irregular-grid workloads.
 
 A step is one pass of the whole hot path: opacity and source function from the populations
 (52 wavelengths), the formal solution over 24 directions by short characteristics with J
 accumulated over angles, rates and statistical equilibrium, and the convergence read-back.
 Metric: point x direction x wavelength updates per second of the step (Gupd/s).
 
+The same JSON line carries the Voronoi-grid measurements (8 atmospheres of 50k-400k sites batched
+against plain per-direction launches, seconds per Lambda iteration on the 215k-site grid), the
+time to convergence on both grids, the adjoint of the mu = 1 map, and the accuracy of the
+32 x 32 x 64 regular and 20k-site Voronoi maps against the 128 x 128 x 256 fine grid.
+
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--extras]
+                    [--no-voronoi] [--no-cpu]
 
 --impl reference times the FP64 CPU oracle on a bounded sample of the same workload.
---extras adds the batched-vs-plain Voronoi sweep of 8 atmospheres and the adjoint timing.
+--extras adds the final synthesis, the small LTE continuum workloads and the accelerated and
+Ng-extrapolated iterations.
 """
 from __future__ import annotations
 
@@ -32,20 +40,37 @@ NDIR = 24
 SCHEME = "plane"          # regular-grid short characteristics: "plane" or "face"
 WORKLOAD = "NLTE Lambda iteration, regular grid 128x128x128, 52 wavelengths, 24 directions"
 
-# DRAM bytes per launch of the dominant kernel from the ncu capture summarised in profiles/,
-# valid only for the kernel source with this hash (else reported as null)
+# DRAM bytes from the ncu captures summarised in profiles/, valid only for the kernel source with
+# this hash (else reported as null)
 PROFILED_FILE = "paper_2306_01041_gb300/csrc/regular_tile.cu"
-PROFILED = {"sc_wave_kernel": {"sha1": "f4fe1598b1f61e1bc98975ba75fa48d3def31502",
-                               "dram_bytes_per_launch": 2.19e9 + 1.23e9},
-            "sc_tile_kernel": {"sha1": None, "dram_bytes_per_launch": None}}
+PROFILED = {"sc_wave_kernel": {"file": PROFILED_FILE, "sha1": None,
+                               "dram_bytes_per_launch": None},
+            "sc_tile_kernel": {"file": PROFILED_FILE, "sha1": None, "dram_bytes_per_launch": None},
+            "batch_sweep_kernel": {"file": "paper_2306_01041_gb300/csrc/batch.cu", "sha1": None,
+                                   "dram_bytes_per_update": None}}
 
-# FP32 FLOPs per point-direction-wavelength update of the sweep: three bilinear interpolations
-# (4 mul + 3 add each), dtau (add, mul), exp and the interval weights (5), the intensity update
-# (2 mul + 2 add + 1), J accumulation (FMA = 2)
-FLOP_PER_UPDATE = 21 + 2 + 6 + 5 + 2
-# FP32 (non-tensor) peak: 152 SMs x 128 lanes x 2 FLOP (FMA) x 2070 MHz
+# Algorithmic FP32 work of one point-direction-wavelength update of the regular sweep, counted in
+# lane operations (an FMA counts once): three bilinear interpolations (6 each), dtau (2), interval
+# weights (4), intensity (3 FMA) and J (1 FMA); plus two SFU operations (exp, reciprocal) not
+# counted.  The bound is one lane operation per FP32 lane per cycle:
+# 152 SMs x 128 lanes x 2070 MHz.
+OPS_PER_UPDATE = 28
 SM_COUNT, LANES, SM_MHZ_MAX = 152, 128, 2070.0
-ALU_PEAK_TFLOPS = SM_COUNT * LANES * 2 * SM_MHZ_MAX * 1e6 / 1e12
+ALU_PEAK_TOPS = SM_COUNT * LANES * SM_MHZ_MAX * 1e6 / 1e12
+# Compulsory HBM bytes of one update of the batched Voronoi sweep at 52 wavelengths: alpha, S and
+# J per (site, wavelength) over 24 directions, the upwind records over the wavelengths, and the
+# intensity written once and gathered twice.
+VOR_BYTES_PER_UPDATE = (12.0 + 24.0 * 24.0 / 52.0) / 24.0 + 4.0
+PEAKS_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+
+
+def hbm_peak():
+    """Measured copy bandwidth of the GB300s (GB/s), else the fallback figure."""
+    try:
+        with open(PEAKS_FILE) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
 
 
 def max_over_ranks(value, device=None):
@@ -135,8 +160,8 @@ def setup_problem(torch, dev, z_stretch=0.0):
     return atm, f, (x, y, z, dx, dy), data, dirs, w
 
 
-def kernel_hash():
-    with open(os.path.join(ROOT, PROFILED_FILE), "rb") as fh:
+def kernel_hash(path=PROFILED_FILE):
+    with open(os.path.join(ROOT, path), "rb") as fh:
         return hashlib.sha1(fh.read()).hexdigest()
 
 
@@ -241,7 +266,7 @@ def run_gpu(args):
     # the formal-solution graph is one persistent wavefront launch (sc_wave_kernel) or, when that
     # path does not apply, one launch per plane step and hemisphere (sc_tile_kernel) plus the two
     # boundary planes; the achieved rate is the interior updates over the graph's event time
-    interior_flops = FLOP_PER_UPDATE * NX * NY * (NZ - 1) * NDIR * nlam
+    interior_ops = OPS_PER_UPDATE * NX * NY * (NZ - 1) * NDIR * nlam
     if args.scheme == "face":
         # face_sweep_kernel, then the fixed-order sum of the two hemispheres' J partials
         kname, per_launch_ms = "face_sweep_kernel", fs_ms
@@ -249,10 +274,10 @@ def run_gpu(args):
         kname, per_launch_ms = "sc_wave_kernel", fs_ms
     else:
         kname, per_launch_ms = "sc_tile_kernel", fs_ms / (2 * (NZ - 1))
-    achieved = interior_flops / (fs_ms * 1e-3) / 1e12
+    achieved = interior_ops / (fs_ms * 1e-3) / 1e12
     traffic = None
     prof = PROFILED.get(kname)
-    if prof and prof["sha1"] == kernel_hash() and prof["dram_bytes_per_launch"]:
+    if prof and prof["sha1"] == kernel_hash(prof["file"]) and prof["dram_bytes_per_launch"]:
         traffic = prof["dram_bytes_per_launch"]
 
     # end to end through the public API with host buffers: H2D of the step's inputs (atmosphere
@@ -294,85 +319,136 @@ def run_gpu(args):
         "launches_per_step": {"source_terms": launches[0], "formal_solution": launches[1],
                               "statistical_equilibrium": launches[2]},
         "roofline": {"bound": "alu", "kernel": kname,
-                     "achieved": round(achieved, 3), "peak": round(ALU_PEAK_TFLOPS, 2),
-                     "unit": "TFLOP/s", "frac": round(achieved / ALU_PEAK_TFLOPS, 4),
+                     "achieved": round(achieved, 3), "peak": round(ALU_PEAK_TOPS, 2),
+                     "unit": "TFLOP/s", "frac": round(achieved / ALU_PEAK_TOPS, 4),
                      "traffic": traffic,
                      "per_launch_ms": round(per_launch_ms, 5),
                      "formal_solution_ms": round(fs_ms, 3),
-                     "peak_note": "FP32 lanes x FMA x max clock (152 x 128 x 2 x 2070 MHz)"},
+                     "interior_gupd_s": round(interior_ops / OPS_PER_UPDATE / fs_ms / 1e6, 2),
+                     "peak_note": "28 FP32 lane operations per update (an FMA counts once) "
+                                  "against one per lane per cycle: 152 SMs x 128 lanes x "
+                                  "2070 MHz, derived from unit counts and the maximum clock"},
         "clocks": clk,
         "breakdown_ms": {"source_terms": round(statistics.mean(p[0] for p in part_times), 3),
                          "formal_solution": round(fs_ms, 3),
                          "statistical_equilibrium": round(statistics.mean(p[1] for p in part_times), 3)},
     }
+    if not args.no_voronoi:
+        work = {s: (g, f, k0) for s, g, f, k0 in voronoi_workload()}
+        vclk = ClockSampler(local)
+        vclk.start()
+        res["voronoi"] = run_voronoi(torch, rt, dev, work)
+        res["voronoi"]["clocks"] = vclk.stop()
+        res["convergence"], conv_pops = convergence_times(torch, rt, dev, work)
+        res["adjoint"] = adjoint_timings(torch, rt, dev, work, conv_pops)
+        res["accuracy"] = accuracy_maps(torch, rt, dev, work)
     if args.extras:
-        res["extras"] = run_extras(torch, rt, dev)
+        res["extras"] = run_extras(torch, rt, dev, None if args.no_voronoi else work)
     if rank == 0 and not args.no_cpu:
-        res["cpu_baseline"] = cpu_baseline(min(args.cpu_lams, nlam))
+        res["cpu_baseline"] = cpu_baseline()
     if rank == 0:
         print(json.dumps(res))
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
-_CPU_INPUTS = {}
+CPU_N = 64          # the oracle's sample: full Lambda iterations on the 64^3 grid
 
 
-def _cpu_inputs():
-    """The oracle's FP64 inputs of the benchmark workload (LTE populations), built once."""
-    if not _CPU_INPUTS:
+class OracleIteration:
+    """The oracle's Lambda iteration as it stands (source terms, formal solution over 24
+    directions, rates, statistical equilibrium; 52 wavelengths) on the n^3 grid of the
+    benchmark's atmosphere, from LTE populations."""
+
+    def __init__(self, n):
+        import oracle
         from oracle.physics import Atom
+        from oracle.solve import RegularGrid as OrcRegular
         from synth import make_atmosphere, model_atom, s4_quadrature
         from synth.atmosphere import regular_fields
         atm = make_atmosphere(0)
-        f, (x, y, z, dx, dy) = regular_fields(NX, NY, NZ, atm)
-        data = model_atom(np.min(f["ne"] / np.sqrt(f["T"])))
-        A = Atom(data, atm.kappa0)
-        pops = A.lte_pops(f["T"], f["ne"], f["nH"])
-        alpha, S = A.alpha_S(f["T"], f["rho"], f["ne"], pops)
+        self.f, (x, y, z, dx, dy) = regular_fields(n, n, n, atm)
+        data = model_atom(np.min(self.f["ne"] / np.sqrt(self.f["T"])))
+        self.A = Atom(data, atm.kappa0)
         dirs, w = s4_quadrature()
-        _CPU_INPUTS.update(alpha=alpha, S=S, dx=dx, dy=dy, z=z, dirs=dirs, w=w)
-    return _CPU_INPUTS
+        self.g = OrcRegular(n, n, n, dx, dy, z, dirs, w, scheme=SCHEME)
+        self.pops = self.A.lte_pops(self.f["T"], self.f["ne"], self.f["nH"])
+        self.nlam = len(data["lam"])
+        self.updates = n ** 3 * NDIR * self.nlam
+        self.cores = oracle.num_threads()
+
+    def step(self):
+        """One iteration; returns its wall time in seconds."""
+        f, A = self.f, self.A
+        t = time.perf_counter()
+        alpha, S = A.alpha_S(f["T"], f["rho"], f["ne"], self.pops)
+        J = self.g.formal_solution(alpha, S)
+        self.pops = A.statistical_equilibrium(A.rate_matrix(f["T"], f["ne"], J), f["nH"])
+        return time.perf_counter() - t
 
 
-def cpu_baseline(nl):
-    """The oracle as it stands on this host's cores: the formal solution (sweep + J) of nl of the
-    52 wavelengths on the benchmark's grid (with the benchmark's scheme), the dominant cost of the
-    step."""
-    import oracle
-    c = _cpu_inputs()
-    alpha, S, dx, dy, z, dirs, w = (c[k] for k in ("alpha", "S", "dx", "dy", "z", "dirs", "w"))
-    pick = np.linspace(0, alpha.shape[0] - 1, nl).astype(int)
-    sweep = oracle.sc_regular_face if SCHEME == "face" else oracle.sc_regular
-    t = time.perf_counter()
-    sweep(NX, NY, NZ, dx, dy, z, dirs, w, alpha[pick], S[pick])
-    dt = time.perf_counter() - t
-    upd = NX * NY * NZ * NDIR * nl
-    scheme = ", face-hitting" if SCHEME == "face" else ""
-    return {"value": round(upd / dt / 1e9, 5), "unit": "Gupd/s", "cores": oracle.num_threads(),
-            "kind": "oracle", "seconds": round(dt, 2),
-            "sample": f"formal solution of {nl} of 52 wavelengths, {NX}x{NY}x{NZ} grid, "
-                      f"24 directions{scheme}"}
+def _cpu_sample_text(n, nlam, cores, reps):
+    scheme = ", face-hitting short characteristics" if SCHEME == "face" else ""
+    return (f"{'mean of ' + str(reps) + ' ' if reps > 1 else 'one '}full Lambda "
+            f"iteration{'s' if reps > 1 else ''} of the oracle (source terms, formal solution, "
+            f"rates, statistical equilibrium; {nlam} wavelengths, 24 directions{scheme}) on the "
+            f"{n}^3 grid of the same atmosphere from LTE; its C sweep on {cores} OpenMP "
+            f"thread{'s' if cores > 1 else ''}, the atom's numpy arithmetic on one core")
+
+
+def cpu_one_thread(n):
+    """One oracle iteration in a subprocess with OMP_NUM_THREADS=1."""
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-iteration", str(n),
+           "--scheme", SCHEME]
+    r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=900)
+    if r.returncode != 0:
+        return {"error": (r.stderr or r.stdout).strip().splitlines()[-1:]}
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline():
+    """The oracle on this host's cores: the mean of three full Lambda iterations on the 64^3 grid
+    (all cores), and one on a single thread."""
+    n = min(CPU_N, NX)
+    it = OracleIteration(n)
+    sec = statistics.mean(it.step() for _ in range(3))
+    return {"value": round(it.updates / sec / 1e9, 5), "unit": "Gupd/s", "cores": it.cores,
+            "kind": "oracle", "seconds_per_iteration": round(sec, 2),
+            "sample": _cpu_sample_text(n, it.nlam, it.cores, 3),
+            "one_thread": cpu_one_thread(n)}
+
+
+def run_cpu_iteration(args):
+    it = OracleIteration(args.cpu_iteration)
+    sec = it.step()
+    print(json.dumps({"value": round(it.updates / sec / 1e9, 5), "unit": "Gupd/s",
+                      "cores": it.cores, "seconds_per_iteration": round(sec, 2),
+                      "sample": _cpu_sample_text(args.cpu_iteration, it.nlam, it.cores, 1)}))
 
 
 def run_reference(args):
     rank, world, local = _env_rank()
     if rank != 0:
         return
-    nl = min(args.cpu_lams, 52)
+    n = min(CPU_N, NX)
+    it = OracleIteration(n)
     for _ in range(args.warmup):
-        cpu_baseline(1)
-    vals = [cpu_baseline(nl) for _ in range(args.steps)]
-    v = statistics.mean(x["value"] for x in vals)
-    sec = statistics.mean(x["seconds"] for x in vals)
-    res = {"impl": "reference", "metric": "formal-solution Gupdates/s (pt*dir*lambda), NLTE Lambda iteration",
+        it.step()
+    secs = [it.step() for _ in range(args.steps)]
+    sec = statistics.mean(secs)
+    v = it.updates / sec / 1e9
+    res = {"impl": "reference",
+           "metric": "formal-solution Gupdates/s (pt*dir*lambda), NLTE Lambda iteration",
            "value": round(v, 5), "unit": "Gupd/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(sec * 1e3, 1), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "grid": [NX, NY, NZ], "wavelengths": 52,
-                      "directions": NDIR, "parallelism": "host cores (OpenMP)"},
-           "cpu_baseline": {"value": round(v, 5), "unit": "Gupd/s", "cores": vals[0]["cores"],
-                            "kind": "oracle", "sample": vals[0]["sample"]},
+           "config": {"workload": WORKLOAD, "grid": [NX, NY, NZ], "wavelengths": it.nlam,
+                      "directions": NDIR, "parallelism": "host cores (OpenMP)",
+                      "sample_grid": [n] * 3},
+           "cpu_baseline": {"value": round(v, 5), "unit": "Gupd/s", "cores": it.cores,
+                            "kind": "oracle",
+                            "sample": _cpu_sample_text(n, it.nlam, it.cores, args.steps)},
            "e2e": {"value": round(v, 5), "unit": "Gupd/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(res))
@@ -382,7 +458,8 @@ VOR_SIZES = [50000, 67000, 90000, 120000, 160000, 215000, 290000, 400000]
 
 
 def _make_vor(args):
-    """One batched-workload atmosphere: seed s, size n; odd seeds rho^0.3, even |dtau/dz|."""
+    """One Voronoi grid of the workloads: site seed s, size n; seeds 1-8 are the batched
+    atmospheres (odd rho^0.3, even |dtau/dz|), later seeds use atmosphere 0 and |dtau/dz|."""
     s, n = args
     sys.path.insert(0, ROOT)
     from synth import make_atmosphere, make_voronoi_grid
@@ -395,138 +472,114 @@ def _make_vor(args):
 def voronoi_workload(sizes=VOR_SIZES, extra=((9, 200000), (10, 20000))):
     """The 8 batched atmospheres (seeds 1-8), plus the 200k-site adjoint grid and the 20k-site LTE
     continuum grid (site seeds 9 and 10, atmosphere seed 0, density from |dtau/dz|), built in
-    parallel."""
+    parallel on the host cores."""
     import multiprocessing as mp
     jobs = list(zip(range(1, len(sizes) + 1), sizes)) + list(extra)
+    jobs.sort(key=lambda j: -j[1])              # largest first: the pool finishes sooner
     with mp.get_context("spawn").Pool(min(len(jobs), os.cpu_count() or 1)) as pool:
-        return pool.map(_make_vor, jobs)
+        return pool.map(_make_vor, jobs, chunksize=1)
 
 
-def run_extras(torch, rt, dev):
-    """Batched persistent Voronoi sweep of 8 atmospheres (50k-400k sites, 52 wavelengths, 24
-    directions) against plain per-direction launches; time to convergence on both grids; the
-    adjoint of the mu = 1 emergent intensity."""
-    from synth import model_atom, s4_quadrature
-    out = {}
-    t0 = time.perf_counter()
-    work = voronoi_workload()
-    out["voronoi_grid_build_s"] = round(time.perf_counter() - t0, 1)
+def _vgrid(rt, g, dirs, w):
+    return rt.VoronoiGrid(g["xyz"], g["nbr_off"], g["nbr_idx"], g["nbr_shift"], g["box"], dirs, w)
+
+
+def _atmos(torch, rt, f, dev):
+    return rt.Atmos(*[torch.tensor(np.ascontiguousarray(f[k]), dtype=torch.float32, device=dev)
+                      for k in ("T", "rho", "ne", "nH")])
+
+
+def run_voronoi(torch, rt, dev, work):
+    """8 atmospheres on Voronoi grids of 50k-400k sites (1.39M), 52 wavelengths, 24 directions:
+    plain per-direction, per-level launches against one persistent all-direction launch per grid
+    and against the batched persistent sweep of all grids; the batched Lambda iteration as one
+    CUDA graph per iteration; seconds per Lambda iteration on the 215k-site grid alone."""
+    from paper_2306_01041_gb300.autotune import tune_batch
+    from synth import make_atmosphere, model_atom, s4_quadrature
     dirs, w = s4_quadrature()
-    extra = {s: (g, f, kappa0) for s, g, f, kappa0 in work if s > 8}
-    work = [x for x in work if x[0] <= 8]
-    grids, atoms, atmoss, alphas, Ss = [], [], [], [], []
-    for s, g, f, kappa0 in work:
-        G = rt.VoronoiGrid(g["xyz"], g["nbr_off"], g["nbr_idx"], g["nbr_shift"], g["box"], dirs, w)
-        data = model_atom(np.min(f["ne"] / np.sqrt(f["T"])))
-        A = rt.Atom(data, kappa0)
-        M = rt.Atmos(*[torch.tensor(f[k], dtype=torch.float32, device=dev)
-                       for k in ("T", "rho", "ne", "nH")])
-        pops = rt.lte_populations(G, A, M)
-        a, sv = rt.source_terms(G, A, M, pops)
-        grids.append(G)
-        atoms.append(A)
-        atmoss.append((M, pops))
+    seeds = sorted(s for s in work if s <= 8)
+    grids = [_vgrid(rt, work[s][0], dirs, w) for s in seeds]
+    fs = [work[s][1] for s in seeds]
+    # one model atom for the batch: the collisional scale from the smallest n_e / sqrt(T) of all
+    # eight atmospheres, the background opacity scale of the recipe's base atmosphere
+    data = model_atom(min(np.min(f["ne"] / np.sqrt(f["T"])) for f in fs))
+    atom = rt.Atom(data, make_atmosphere(0).kappa0)
+    atms = [_atmos(torch, rt, f, dev) for f in fs]
+    pops0 = [rt.lte_populations(G, atom, M) for G, M in zip(grids, atms)]
+    alphas, Ss = [], []
+    for G, M, p in zip(grids, atms, pops0):
+        a, sv = rt.source_terms(G, atom, M, p)
         alphas.append(a)
         Ss.append(sv)
-    nlam = alphas[0].shape[0]
-    upd = sum(g.npt for g in grids) * NDIR * nlam
-
-    def timeit(fn, reps=3):
-        fn()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
-            fn()
-        e1.record()
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / reps
-
+    nlam = atom.nlam
+    upd = sum(G.npt for G in grids) * NDIR * nlam
     Jp = [torch.empty_like(a) for a in alphas]
     os.environ["RT_VORONOI_SWEEP"] = "levels"      # plain per-direction, per-level launches
-    ms_plain = timeit(lambda: [rt.formal_solution(g, a, sv, J=j)
-                               for g, a, sv, j in zip(grids, alphas, Ss, Jp)])
-    del os.environ["RT_VORONOI_SWEEP"]
+    try:
+        ms_plain = _events(torch, lambda: [rt.formal_solution(G, a, sv, J=j)
+                                           for G, a, sv, j in zip(grids, alphas, Ss, Jp)])
+    finally:
+        del os.environ["RT_VORONOI_SWEEP"]
     Js = [torch.empty_like(a) for a in alphas]      # one persistent launch per grid, in turn
-    ms_single = timeit(lambda: [rt.formal_solution(g, a, sv, J=j)
-                                for g, a, sv, j in zip(grids, alphas, Ss, Js)])
-    from paper_2306_01041_gb300.autotune import tune_batch
+    ms_single = _events(torch, lambda: [rt.formal_solution(G, a, sv, J=j)
+                                        for G, a, sv, j in zip(grids, alphas, Ss, Js)])
     batch, choice = tune_batch(grids, alphas, Ss, nlam)
     Jb = [torch.empty_like(a) for a in alphas]
-    ms_batch = timeit(lambda: batch.formal_solution(alphas, Ss, Js=Jb))
+    ms_batch = _events(torch, lambda: batch.formal_solution(alphas, Ss, Js=Jb), reps=5)
     diff = max(float(((b - p).abs() / p.abs().clamp_min(1e-30)).max()) for b, p in zip(Jb, Jp))
-    out["voronoi_batch"] = {
-        "atmospheres": len(grids), "sites": [g.npt for g in grids],
-        "levels_max": [g.max_levels for g in grids], "wavelengths": nlam, "directions": NDIR,
-        "plain_ms": round(ms_plain, 2), "batched_ms": round(ms_batch, 2),
-        "per_grid_persistent_ms": round(ms_single, 2),
-        "plain_gupd_s": round(upd / ms_plain / 1e6, 3),
-        "per_grid_persistent_gupd_s": round(upd / ms_single / 1e6, 3),
-        "batched_gupd_s": round(upd / ms_batch / 1e6, 3),
-        "speedup": round(ms_plain / ms_batch, 2), "max_rel_diff_batched_vs_plain": diff,
-        "autotuned": choice}
-    # one batched Lambda iteration captured as a CUDA graph
-    s_cap = torch.cuda.Stream()
-    s_cap.wait_stream(torch.cuda.current_stream())
-    graph = torch.cuda.CUDAGraph()
-    bufs = [(torch.empty_like(a), torch.empty_like(a)) for a in alphas]
-
-    def iteration(stream):
-        for (M, pops), G, A, (ab, sb) in zip(atmoss, grids, atoms, bufs):
-            a, sv = rt.source_terms(G, A, M, pops, stream=stream)
-            ab.copy_(a)
-            sb.copy_(sv)
-        batch.formal_solution([b[0] for b in bufs], [b[1] for b in bufs], Js=Jb, stream=stream)
-        for (M, pops), G, A, J in zip(atmoss, grids, atoms, Jb):
-            rt.statistical_equilibrium(G, A, M, J, pops, stream=stream)
-    with torch.cuda.stream(s_cap):
-        iteration(s_cap)
-        s_cap.synchronize()
-        try:
-            with torch.cuda.graph(graph, stream=s_cap):
-                iteration(s_cap)
-            graph_ok = True
-        except Exception as exc:   # report, do not fail the benchmark
-            graph_ok = repr(exc)
-    torch.cuda.current_stream().wait_stream(s_cap)
-    if graph_ok is True:
-        ms_graph = timeit(lambda: graph.replay())
-        out["voronoi_batch"]["graph_iteration_ms"] = round(ms_graph, 2)
-    else:
-        out["voronoi_batch"]["graph_iteration_error"] = graph_ok
-    # time to convergence: the 128^3 regular grid and the 215k-site irregular grid
-    out["convergence"] = convergence_times(torch, rt, dev, grids[5], atoms[5], atmoss[5])
-    out["adjoint"] = adjoint_timing(torch, rt, dev)
-    out["adjoint_voronoi_200k"] = voronoi_adjoint_timing(torch, rt, dev, *extra[9], dirs, w)
-    out["lte_continuum"] = lte_continuum_timing(torch, rt, dev, *extra[10], dirs, w)
-    out["final_synthesis"] = synthesis_timing(torch, rt, dev, *extra[9], dirs, w)
-    return out
-
-
-def synthesis_timing(torch, rt, dev, g, f, kappa0, dirs, w):
-    """The paper's final synthesis from the 200k-site grid (populations at LTE) to the 128^3
-    mesh: two-nearest table (host, once), interpolation of the populations, source terms and the
-    vertical long-characteristics formal solution on the mesh (52 wavelengths)."""
-    from synth import make_atmosphere, model_atom
-    from synth.atmosphere import regular_fields
-    atm = make_atmosphere(0)
-    mf, (x, y, z, dx, dy) = regular_fields(NX, NY, NZ, atm)
-    G = rt.VoronoiGrid(g["xyz"], g["nbr_off"], g["nbr_idx"], g["nbr_shift"], g["box"], dirs, w)
-    mesh = rt.RegularGrid(NX, NY, NZ, dx, dy, z, dirs, w)
-    A = rt.Atom(model_atom(np.min(mf["ne"] / np.sqrt(mf["T"]))), atm.kappa0)
-    sv = rt.Atmos(*[torch.tensor(f[k], dtype=torch.float32, device=dev)
-                    for k in ("T", "rho", "ne", "nH")])
-    mv = rt.Atmos(*[torch.tensor(mf[k], dtype=torch.float32, device=dev)
-                    for k in ("T", "rho", "ne", "nH")])
-    site_pops = rt.lte_populations(G, A, sv)
+    # the batched Lambda iteration, one CUDA graph per iteration (host-timed, with the read-back
+    # of the convergence scalar every iteration)
+    pops = [p.clone() for p in pops0]
+    batch.lambda_iterate(atom, atms, pops, max_iter=1, tol=0.0)   # graph capture and scratch
+    for q, p in zip(pops, pops0):
+        q.copy_(p)
+    torch.cuda.synchronize()
     t = time.perf_counter()
-    idw = rt.IDW(G, mesh)
-    build_s = time.perf_counter() - t
-    res = {"sites": G.npt, "mesh": [NX, NY, NZ], "table_build_s": round(build_s, 3),
-           "interpolate_ms": round(_events(torch, lambda: idw.interpolate(site_pops)), 3),
-           "final_synthesis_ms": round(_events(torch, lambda: rt.final_synthesis(
-               idw, mesh, A, mv, site_pops)), 3)}
-    return res
+    it, hist, _ = batch.lambda_iterate(atom, atms, pops, max_iter=5, tol=0.0)
+    s_batch_iter = (time.perf_counter() - t) / it
+    # the 215k-site grid alone (its own atmosphere's atom)
+    k215 = seeds.index(6)
+    G6, f6 = grids[k215], fs[k215]
+    A6 = rt.Atom(model_atom(np.min(f6["ne"] / np.sqrt(f6["T"]))), work[6][2])
+    M6 = atms[k215]
+    p6 = rt.lte_populations(G6, A6, M6)
+    rt.lambda_iterate(G6, A6, M6, p6, max_iter=1, tol=0.0)
+    p6 = rt.lte_populations(G6, A6, M6)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    it6, _, _ = rt.lambda_iterate(G6, A6, M6, p6, max_iter=5, tol=0.0)
+    s_iter_215 = (time.perf_counter() - t) / it6
+    peak, peak_src = hbm_peak()
+    achieved = VOR_BYTES_PER_UPDATE * upd / (ms_batch * 1e-3) / 1e9
+    traffic = None
+    prof = PROFILED.get("batch_sweep_kernel")
+    if prof and prof["sha1"] == kernel_hash(prof["file"]) and prof["dram_bytes_per_update"]:
+        traffic = prof["dram_bytes_per_update"] * upd
+    return {
+        "workload": "8 atmospheres on Voronoi grids (sites from rho^0.3 and |dtau/dz|), one model "
+                    "atom, 52 wavelengths, 24 directions, populations at LTE",
+        "atmospheres": len(grids), "sites": [G.npt for G in grids],
+        "levels_max": [G.max_levels for G in grids], "updates_per_formal_solution": upd,
+        "plain_ms": round(ms_plain, 3), "plain_gupd_s": round(upd / ms_plain / 1e6, 3),
+        "per_grid_persistent_ms": round(ms_single, 3),
+        "per_grid_persistent_gupd_s": round(upd / ms_single / 1e6, 3),
+        "batched_ms": round(ms_batch, 3), "batched_gupd_s": round(upd / ms_batch / 1e6, 3),
+        "speedup_batched_vs_plain": round(ms_plain / ms_batch, 2),
+        "max_rel_diff_batched_vs_plain": diff, "autotuned": choice,
+        "batched_lambda_iteration_s": round(s_batch_iter, 5),
+        "batched_lambda_iteration_note": "rt_batch_lambda_iterate, one CUDA graph per iteration, "
+                                         "host wall time per iteration including the read-back",
+        "grid_215k": {"sites": G6.npt, "levels_max": G6.max_levels,
+                      "s_per_lambda_iteration": round(s_iter_215, 5),
+                      "gupd_s": round(G6.npt * NDIR * nlam / s_iter_215 / 1e9, 3)},
+        "roofline": {"bound": "hbm", "kernel": "batch_sweep_kernel",
+                     "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "bytes_per_update": round(VOR_BYTES_PER_UPDATE, 3),
+                     "note": f"compulsory bytes per update x updates / event time of the whole "
+                             f"batched formal solution (transposes, sweep, J reduction); peak "
+                             f"{peak_src} copy bandwidth"},
+    }
 
 
 def run_iterate(args):
@@ -657,30 +710,168 @@ def _events(torch, fn, reps=3):
     return e0.elapsed_time(e1) / reps
 
 
-def voronoi_adjoint_timing(torch, rt, dev, g, f, kappa0, dirs, w):
-    """Emergent mu = 1 intensity and its adjoint at the line core and both continua on the
-    200k-site grid, populations at LTE."""
-    from synth import model_atom
-    G = rt.VoronoiGrid(g["xyz"], g["nbr_off"], g["nbr_idx"], g["nbr_shift"], g["box"], dirs, w)
-    data = model_atom(np.min(f["ne"] / np.sqrt(f["T"])))
-    A = rt.Atom(data, kappa0)
-    M = rt.Atmos(*[torch.tensor(f[k], dtype=torch.float32, device=dev)
-                   for k in ("T", "rho", "ne", "nH")])
-    pops = rt.lte_populations(G, A, M)
-    a, sv = rt.source_terms(G, A, M, pops)
-    core = int(np.argmin(np.abs(np.asarray(data["lam"]) - data["lam0"])))
-    pick = [core, len(data["lam"]) - 2, len(data["lam"]) - 1]
-    a3, s3 = a[pick].contiguous(), sv[pick].contiguous()
-    gI = torch.ones((3, G.ntop), device=dev)
-    res = {"sites": G.npt, "top_sites": G.ntop,
-           "emergent_ms": round(_events(torch, lambda: rt.emergent_intensity(
-               G, (0.0, 0.0, 1.0), a3, s3)), 3)}
-    for stride in (1, 8):
-        res[f"adjoint_stride_{stride}_ms"] = round(_events(torch, lambda: rt.formal_solution_adjoint(
-            G, (0.0, 0.0, 1.0), a3, s3, gI, ckpt_stride=stride)), 3)
-        res[f"adjoint_stride_{stride}_workspace_MB"] = round(
-            rt.lib().rt_adjoint_workspace_size(G.handle, 3, stride) / 2 ** 20, 1)
+def convergence_times(torch, rt, dev, work):
+    """Time to convergence (max |dn/n| < 1e-3 from LTE) of the Lambda iteration and of the
+    accelerated one on the 128^3 regular grid and on the 215k-site Voronoi grid; returns the
+    timings and the converged populations of the plain iteration."""
+    from synth import make_atmosphere, model_atom, s4_quadrature
+    from synth.atmosphere import regular_fields
+    res, out = {}, {}
+    atm = make_atmosphere(0)
+    f, (x, y, z, dx, dy) = regular_fields(NX, NY, NZ, atm)
+    dirs, w = s4_quadrature()
+    g = rt.RegularGrid(NX, NY, NZ, dx, dy, z, dirs, w)
+    A = rt.Atom(model_atom(np.min(f["ne"] / np.sqrt(f["T"]))), atm.kappa0)
+    M = _atmos(torch, rt, f, dev)
+    g6, f6, k6 = work[6]
+    G6 = _vgrid(rt, g6, dirs, w)
+    A6 = rt.Atom(model_atom(np.min(f6["ne"] / np.sqrt(f6["T"]))), k6)
+    M6 = _atmos(torch, rt, f6, dev)
+    for name, (G, AA, MM) in ((f"regular_{NX}x{NY}x{NZ}", (g, A, M)),
+                              (f"voronoi_{G6.npt}_sites", (G6, A6, M6))):
+        for method, fn in (("lambda", rt.lambda_iterate), ("accelerated", rt.lambda_iterate_ali)):
+            pops = rt.lte_populations(G, AA, MM)
+            fn(G, AA, MM, pops, max_iter=1, tol=1e-3)       # graph capture and scratch, untimed
+            pops = rt.lte_populations(G, AA, MM)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            it, hist, conv = fn(G, AA, MM, pops, max_iter=300, tol=1e-3)
+            dt = time.perf_counter() - t
+            res[f"{name}_{method}"] = {"iterations": it, "converged": bool(conv),
+                                       "seconds": round(dt, 4),
+                                       "s_per_iteration": round(dt / it, 5),
+                                       "final_change": float(hist[-1])}
+            if method == "lambda":
+                out[name] = (G, AA, MM, pops)
+    res["note"] = ("from LTE populations until max |dn/n| < 1e-3 (at most 300 iterations); host "
+                   "wall time, one CUDA graph per iteration, a read-back every iteration")
+    return res, out
+
+
+def _pick3(atom_data):
+    """The line core and the two continuum wavelengths of the atom."""
+    lam = np.asarray(atom_data["lam"])
+    return [int(np.argmin(np.abs(lam - atom_data["lam0"]))), len(lam) - 2, len(lam) - 1]
+
+
+def _gradient_timing(torch, rt, G, A, M, pops, pick, stride):
+    """Gradient of the sum of the mu = 1 map at three wavelengths with respect to T (through
+    alpha and S at fixed populations), alpha and S: emergent map, adjoint sweep, chain rule."""
+    alpha, S = rt.source_terms(G, A, M, pops)
+    a3, s3 = alpha[pick].contiguous(), S[pick].contiguous()
+    gI = torch.ones((3, G.ntop), device=alpha.device)
+    ga_full = torch.zeros_like(alpha)
+    gs_full = torch.zeros_like(alpha)
+
+    def grad():
+        rt.emergent_intensity(G, (0.0, 0.0, 1.0), a3, s3)
+        ga, gs = rt.formal_solution_adjoint(G, (0.0, 0.0, 1.0), a3, s3, gI, ckpt_stride=stride)
+        ga_full[pick] = ga
+        gs_full[pick] = gs
+        return rt.source_terms_adjoint(G, A, M, pops, ga_full, gs_full)
+    ms = _events(torch, grad)
+    ws = rt.lib().rt_adjoint_workspace_size(G.handle, 3, stride)
+    return {"ms": round(ms, 3), "checkpoint_stride": stride, "workspace_MB": round(ws / 2 ** 20, 1)}
+
+
+def adjoint_timings(torch, rt, dev, work, conv):
+    """Gradient of the mu = 1 emergent map at the line core and both continua with respect to T,
+    alpha and S at every point, populations at their converged NLTE values: the 128^3 regular
+    grid and the 200k-site Voronoi grid."""
+    from synth import make_atmosphere, model_atom
+    res = {}
+    name = f"regular_{NX}x{NY}x{NZ}"
+    G, A, M, pops = conv[name]
+    data = model_atom()
+    pick = _pick3(data)
+    res[name] = [_gradient_timing(torch, rt, G, A, M, pops, pick, st) for st in (1, 11)]
+    from synth import s4_quadrature
+    dirs, w = s4_quadrature()
+    g9, f9, k9 = work[9]
+    G9 = _vgrid(rt, g9, dirs, w)
+    A9 = rt.Atom(model_atom(np.min(f9["ne"] / np.sqrt(f9["T"]))), k9)
+    M9 = _atmos(torch, rt, f9, dev)
+    p9 = rt.lte_populations(G9, A9, M9)
+    it, _, conv9 = rt.lambda_iterate(G9, A9, M9, p9, max_iter=300, tol=1e-3)
+    res[f"voronoi_{G9.npt}_sites"] = [_gradient_timing(torch, rt, G9, A9, M9, p9, pick, st)
+                                      for st in (1, 8)]
+    res["voronoi_converged_in"] = it
+    res["note"] = ("mu = 1 map forward, adjoint sweep (FP64 on the device), chain rule to T at "
+                   "fixed populations; CUDA events")
     return res
+
+
+def accuracy_maps(torch, rt, dev, work):
+    """LTE continuum at 500 nm, mu = 1 maps: the 32 x 32 x 64 regular grid and the 20k-site
+    Voronoi grid (sampled from |dtau/dz|) against the 128 x 128 x 256 fine grid, as the RMS of the
+    relative difference at the 32 x 32 shared pixels.  The Voronoi grid twice: its emergent-layer
+    sites resampled to 32 x 32 pixels by two-nearest inverse-distance weighting, and the paper's
+    procedure (the opacity at the sites interpolated back to the fine mesh by two-nearest inverse
+    distance weighting, the mesh's own source function, the vertical formal solution there)."""
+    from synth import make_atmosphere, s4_quadrature
+    from synth.atmosphere import regular_fields
+    atm = make_atmosphere(0)
+    dirs, w = s4_quadrature()
+    mu1 = (0.0, 0.0, 1.0)
+
+    def regular(n):
+        f, (x, y, z, dx, dy) = regular_fields(n, n, 2 * n, atm)
+        G = rt.RegularGrid(n, n, 2 * n, dx, dy, z, dirs, w)
+        a, sv = rt.source_terms_lte(torch.tensor(f["T"], dtype=torch.float32, device=dev),
+                                    torch.tensor(f["rho"], dtype=torch.float32, device=dev),
+                                    atm.kappa0, 500e-9)
+        a, sv = a[None].contiguous(), sv[None].contiguous()
+        return G, a, sv, rt.emergent_map(G, mu1, a, sv, n, n)[0].reshape(n, n)
+    Gf, af, sf, fine = regular(128)
+    _, _, _, m32 = regular(32)
+    g10, f10, _ = work[10]
+    G10 = _vgrid(rt, g10, dirs, w)
+    av, sv = rt.source_terms_lte(torch.tensor(f10["T"], dtype=torch.float32, device=dev),
+                                 torch.tensor(f10["rho"], dtype=torch.float32, device=dev),
+                                 atm.kappa0, 500e-9)
+    av, sv = av[None].contiguous(), sv[None].contiguous()
+    native = rt.emergent_map(G10, mu1, av, sv, 32, 32)[0].reshape(32, 32)
+    idw = rt.IDW(G10, Gf)
+    synth_map = rt.emergent_map(Gf, mu1, idw.interpolate(av), sf, 128, 128)[0].reshape(128, 128)
+    ref = fine[::4, ::4]
+
+    def rms(m, r):
+        return float(torch.sqrt(torch.mean((m.double() / r.double() - 1.0) ** 2)))
+    e_reg, e_nat = rms(m32, ref), rms(native, ref)
+    e_fs, e_fs128 = rms(synth_map[::4, ::4], ref), rms(synth_map, fine)
+    return {"workload": "LTE continuum at 500 nm, mu = 1 emergent maps",
+            "reference": "128x128x256 regular grid", "pixels": [32, 32],
+            "rms_rel_diff": {"regular_32x32x64": round(e_reg, 5),
+                             "voronoi_20k_native": round(e_nat, 5),
+                             "voronoi_20k_final_synthesis": round(e_fs, 5),
+                             "voronoi_20k_final_synthesis_128x128": round(e_fs128, 5)},
+            "ratio_voronoi_native_to_regular": round(e_nat / e_reg, 3),
+            "ratio_voronoi_final_synthesis_to_regular": round(e_fs / e_reg, 3),
+            "voronoi_top_sites": G10.ntop,
+            "fine_map_rms_contrast": round(float(fine.double().std() / fine.double().mean()), 4)}
+
+
+def synthesis_timing(torch, rt, dev, g, f, kappa0, dirs, w):
+    """The paper's final synthesis from the 200k-site grid (populations at LTE) to the 128^3
+    mesh: two-nearest table (host, once), interpolation of the populations, source terms and the
+    vertical long-characteristics formal solution on the mesh (52 wavelengths)."""
+    from synth import make_atmosphere, model_atom
+    from synth.atmosphere import regular_fields
+    atm = make_atmosphere(0)
+    mf, (x, y, z, dx, dy) = regular_fields(NX, NY, NZ, atm)
+    G = _vgrid(rt, g, dirs, w)
+    mesh = rt.RegularGrid(NX, NY, NZ, dx, dy, z, dirs, w)
+    A = rt.Atom(model_atom(np.min(mf["ne"] / np.sqrt(mf["T"]))), atm.kappa0)
+    sv = _atmos(torch, rt, f, dev)
+    mv = _atmos(torch, rt, mf, dev)
+    site_pops = rt.lte_populations(G, A, sv)
+    t = time.perf_counter()
+    idw = rt.IDW(G, mesh)
+    build_s = time.perf_counter() - t
+    return {"sites": G.npt, "mesh": [NX, NY, NZ], "table_build_s": round(build_s, 3),
+            "interpolate_ms": round(_events(torch, lambda: idw.interpolate(site_pops)), 3),
+            "final_synthesis_ms": round(_events(torch, lambda: rt.final_synthesis(
+                idw, mesh, A, mv, site_pops)), 3)}
 
 
 def lte_continuum_timing(torch, rt, dev, g, f, kappa0, dirs, w):
@@ -692,7 +883,7 @@ def lte_continuum_timing(torch, rt, dev, g, f, kappa0, dirs, w):
     atm = make_atmosphere(0)
     fr, (x, y, z, dx, dy) = regular_fields(32, 32, 64, atm)
     gr = rt.RegularGrid(32, 32, 64, dx, dy, z, dirs, w)
-    G = rt.VoronoiGrid(g["xyz"], g["nbr_off"], g["nbr_idx"], g["nbr_shift"], g["box"], dirs, w)
+    G = _vgrid(rt, g, dirs, w)
     for name, grid, ff in (("regular_32x32x64", gr, fr), ("voronoi_20k", G, f)):
         al, S = rt.source_terms_lte(torch.tensor(ff["T"], dtype=torch.float32, device=dev),
                                     torch.tensor(ff["rho"], dtype=torch.float32, device=dev),
@@ -705,68 +896,32 @@ def lte_continuum_timing(torch, rt, dev, g, f, kappa0, dirs, w):
     return res
 
 
-def convergence_times(torch, rt, dev, vgrid, vatom, vatm):
-    from synth import make_atmosphere, model_atom, s4_quadrature
-    from synth.atmosphere import regular_fields
-    res = {}
-    atm = make_atmosphere(0)
-    f, (x, y, z, dx, dy) = regular_fields(NX, NY, NZ, atm)
-    data = model_atom(np.min(f["ne"] / np.sqrt(f["T"])))
+def run_extras(torch, rt, dev, work=None):
+    """The final synthesis, the small LTE continuum workloads and the Ng-extrapolated
+    iterations."""
+    from synth import s4_quadrature
+    if work is None:
+        work = {s: (g, f, k0) for s, g, f, k0 in voronoi_workload()}
     dirs, w = s4_quadrature()
-    g = rt.RegularGrid(NX, NY, NZ, dx, dy, z, dirs, w)
-    A = rt.Atom(data, atm.kappa0)
-    M = rt.Atmos(*[torch.tensor(f[k], dtype=torch.float32, device=dev)
-                   for k in ("T", "rho", "ne", "nH")])
-    for name, (G, AA, MM) in (("regular_128^3", (g, A, M)),
-                              ("voronoi_%d_sites" % vgrid.npt, (vgrid, vatom, vatm[0]))):
-        for method, fn, ngp in (("lambda", rt.lambda_iterate, 0), ("ali", rt.lambda_iterate_ali, 0),
-                                ("lambda_ng", rt.lambda_iterate, 3),
-                                ("ali_ng", rt.lambda_iterate_ali, 3)):
-            pops = rt.lte_populations(G, AA, MM)
-            fn(G, AA, MM, pops, max_iter=1, tol=1e-3, ng_period=ngp)   # first-call set-up
-            pops = rt.lte_populations(G, AA, MM)
-            torch.cuda.synchronize()
-            t = time.perf_counter()
-            it, hist, conv = fn(G, AA, MM, pops, max_iter=300, tol=1e-3, ng_period=ngp)
-            dt = time.perf_counter() - t
-            res[f"{name}_{method}"] = {"iterations": it, "converged": bool(conv),
-                                       "seconds": round(dt, 3), "s_per_iteration": round(dt / it, 5),
-                                       "final_change": float(hist[-1])}
-    return res
-
-
-def adjoint_timing(torch, rt, dev):
-    """Gradient of the mu = 1 emergent map at the line core and both continua on 128^3."""
-    from synth import make_atmosphere, model_atom, s4_quadrature
+    out = {"final_synthesis": synthesis_timing(torch, rt, dev, *work[9], dirs, w),
+           "lte_continuum": lte_continuum_timing(torch, rt, dev, *work[10], dirs, w)}
+    from synth import make_atmosphere, model_atom
     from synth.atmosphere import regular_fields
     atm = make_atmosphere(0)
     f, (x, y, z, dx, dy) = regular_fields(NX, NY, NZ, atm)
-    data = model_atom(np.min(f["ne"] / np.sqrt(f["T"])))
-    dirs, w = s4_quadrature()
     g = rt.RegularGrid(NX, NY, NZ, dx, dy, z, dirs, w)
-    A = rt.Atom(data, atm.kappa0)
-    M = rt.Atmos(*[torch.tensor(f[k], dtype=torch.float32, device=dev)
-                   for k in ("T", "rho", "ne", "nH")])
-    pops = rt.lte_populations(g, A, M)
-    a, sv = rt.source_terms(g, A, M, pops)
-    core = int(np.argmin(np.abs(np.asarray(data["lam"]) - data["lam0"])))
-    pick = [core, len(data["lam"]) - 2, len(data["lam"]) - 1]
-    a3, s3 = a[pick].contiguous(), sv[pick].contiguous()
-    gI = torch.ones((3, g.ntop), device=dev)
-    res = {}
-    for stride in (1, 11):
-        rt.formal_solution_adjoint(g, (0.0, 0.0, 1.0), a3, s3, gI, ckpt_stride=stride)
+    A = rt.Atom(model_atom(np.min(f["ne"] / np.sqrt(f["T"]))), atm.kappa0)
+    M = _atmos(torch, rt, f, dev)
+    for name, fn in (("lambda_ng3", rt.lambda_iterate), ("accelerated_ng3", rt.lambda_iterate_ali)):
+        pops = rt.lte_populations(g, A, M)
+        fn(g, A, M, pops, max_iter=1, tol=1e-3, ng_period=3)
+        pops = rt.lte_populations(g, A, M)
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(3):
-            rt.formal_solution_adjoint(g, (0.0, 0.0, 1.0), a3, s3, gI, ckpt_stride=stride)
-        e1.record()
-        torch.cuda.synchronize()
-        res[f"stride_{stride}_ms"] = round(e0.elapsed_time(e1) / 3, 3)
-        res[f"stride_{stride}_workspace_MB"] = round(
-            rt.lib().rt_adjoint_workspace_size(g.handle, 3, stride) / 2 ** 20, 1)
-    return res
+        t = time.perf_counter()
+        it, hist, conv = fn(g, A, M, pops, max_iter=300, tol=1e-3, ng_period=3)
+        out[f"regular_{name}"] = {"iterations": it, "converged": bool(conv),
+                                  "seconds": round(time.perf_counter() - t, 4)}
+    return out
 
 
 def main():
@@ -776,8 +931,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--extras", action="store_true")
-    ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-lams", type=int, default=52)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle's CPU baseline")
+    ap.add_argument("--no-voronoi", action="store_true",
+                    help="only the regular-grid line (no Voronoi, convergence, adjoint, accuracy)")
+    ap.add_argument("--cpu-iteration", type=int, default=0,
+                    help="print the oracle's time for one Lambda iteration on an N^3 grid")
     ap.add_argument("--nx", type=int, default=128,
                     help="grid size per axis (profiling uses smaller cases; the benchmark is 128)")
     ap.add_argument("--voronoi-batch", type=int, default=0,
@@ -809,6 +967,9 @@ def main():
         WORKLOAD += ", face-hitting short characteristics"
     if args.warmup < 3:
         args.warmup = 3
+    if args.cpu_iteration:
+        run_cpu_iteration(args)
+        return
     if args.voronoi_batch:
         run_voronoi_batch(args)
         return

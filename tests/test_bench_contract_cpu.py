@@ -10,7 +10,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def _line(*extra):
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                          "--nx", "24", "--steps", "1", "--warmup", "3", "--cpu-lams", "2", *extra],
+                          "--nx", "16", "--steps", "1", "--warmup", "3", *extra],
                          capture_output=True, text=True, timeout=600, cwd=ROOT, check=True)
     lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
     assert len(lines) == 1, out.stdout
@@ -25,10 +25,10 @@ def test_reference_arm_line():
         assert k in r, k
     assert r["impl"] == "reference" and r["value"] > 0 and r["steps"] == 1 and r["warmup"] == 3
     assert r["higher_is_better"] is True and r["scaling"] == "weak" and r["vs_baseline"] is None
-    assert r["config"]["grid"] == [24, 24, 24] and "24x24x24" in r["config"]["workload"]
+    assert r["config"]["grid"] == [16, 16, 16] and "16x16x16" in r["config"]["workload"]
     cb = r["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == r["value"]
-    assert "24x24x24" in cb["sample"] and "2 of 52" in cb["sample"]
+    assert "16^3 grid" in cb["sample"] and "full Lambda iteration" in cb["sample"]
     assert r["e2e"] == {"value": r["value"], "unit": r["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
 
@@ -36,3 +36,13 @@ def test_reference_arm_line():
 def test_reference_arm_follows_the_scheme():
     r = _line("--scheme", "face")
     assert "face-hitting" in r["config"]["workload"] and "face-hitting" in r["cpu_baseline"]["sample"]
+
+
+def test_one_thread_oracle_iteration():
+    """The single-thread figure of the CPU baseline: one oracle iteration in a process whose
+    OpenMP runtime has one thread."""
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--cpu-iteration", "12"],
+                         capture_output=True, text=True, timeout=600, cwd=ROOT, check=True, env=env)
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    assert r["cores"] == 1 and r["value"] > 0 and "12^3 grid" in r["sample"]
