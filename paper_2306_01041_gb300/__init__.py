@@ -7,7 +7,8 @@ Build the library first (``python -c "import __graft_entry__ as g; g.build()"`` 
 from ._lib import (RT_BC_ARRAY, RT_BC_THERMAL, RT_BC_ZERO, RT_SC_FACE,  # noqa: F401
                    RT_SC_PLANE, RTError, lib)
 from .api import (IDW, Atmos, Atom, Batch, EmergentIntensity, Grid, RegularGrid,  # noqa: F401
-                  VoronoiGrid, emergent_intensity, final_synthesis, formal_solution,
+                  VoronoiGrid, emergent_intensity, emergent_map, final_synthesis,
+                  formal_solution,
                   formal_solution_adjoint,
                   kernel_launches, lambda_iterate, lambda_iterate_ali, lambda_star,
                   lte_populations, ng_extrapolate, sample_sites, source_terms,

@@ -57,7 +57,7 @@ def test_ragged_random_multi_lambda(rt, periodic, bc):
 
 
 def test_constant_source_closed_form(rt):
-    """C-P1 on the GPU: I = I0 exp(-tau) + S (1 - exp(-tau)) along every ray."""
+    """Constant alpha and S on the GPU: I = I0 exp(-tau) + S (1 - exp(-tau)) along every ray."""
     nx, ny, nz = 8, 8, 40
     z = np.linspace(0.0, 4.0, nz)
     dirs, w = s4_quadrature()

@@ -157,3 +157,16 @@ def test_face_scheme_and_site_sampling_reject_bad_arguments_on_host(librt):
     assert call(xyz=ctypes.c_void_p(260)) == L.RT_EINVAL
     assert b"aligned" in lib.rt_last_error()
     assert rt.kernel_launches() == n0
+
+
+def test_package_reexports_the_binding():
+    """Every public function and class of the binding (api.py) is reachable from the package."""
+    import inspect
+
+    import paper_2306_01041_gb300 as rt
+    from paper_2306_01041_gb300 import api
+    public = [n for n, v in vars(api).items()
+              if not n.startswith("_") and (inspect.isfunction(v) or inspect.isclass(v))
+              and getattr(v, "__module__", "") == api.__name__]
+    missing = [n for n in public if not hasattr(rt, n)]
+    assert not missing, missing

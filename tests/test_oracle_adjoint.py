@@ -1,4 +1,4 @@
-"""C-P9 pins of the oracle's hand-derived adjoint sweeps (Eq. 2 differentiated): central finite
+"""Pins of the oracle's hand-derived adjoint sweeps (Eq. 2 differentiated): central finite
 differences in FP64 and the exact linearity of I in S (CPU only)."""
 import numpy as np
 import pytest

@@ -55,7 +55,7 @@ def _grid_z(nz, nonuniform=True, L=1.0, seed=3):
     return z * (L / z[-1])
 
 
-# ---- C-P1: constant S and alpha: I = I0 exp(-tau) + S (1 - exp(-tau)) exactly ------------------
+# ---- constant S and alpha: I = I0 exp(-tau) + S (1 - exp(-tau)) exactly (Eq. 2) ---------------
 @pytest.mark.parametrize("bc", [1, 2])
 def test_constant_source_exact(bc):
     nx, ny, nz = 5, 4, 9
@@ -77,7 +77,7 @@ def test_constant_source_exact(bc):
                                    atol=1e-15)
 
 
-# ---- C-P2: S linear along every ray is integrated exactly --------------------------------------
+# ---- S linear along every ray is integrated exactly (Eq. 2, linear S) --------------------------
 def test_linear_source_exact():
     """S = a + b z, alpha constant: I = S - b mu_z / alpha solves dI/dtau = S - I on every ray;
     with that inflow on both walls the scheme must reproduce it at every point."""
@@ -98,7 +98,7 @@ def test_linear_source_exact():
     np.testing.assert_allclose(J[0], S[0] - B * np.sum(w * dirs[:, 2]) / a0, rtol=1e-12)
 
 
-# ---- C-P3: horizontally homogeneous slab = the exact 1D solution on the slanted ray ----------
+# ---- horizontally homogeneous slab = the exact 1D solution on the slanted ray ----------------
 def _exact_slab(z, mu, alpha_f, tau_f, S_f, inflow):
     """Exact Eq. 2 along a ray of direction cosine mu through a slab (scipy quadrature)."""
     out = []
@@ -143,7 +143,7 @@ def test_plane_parallel_reduction_converges():
     assert errs[2] < 2e-3
 
 
-# ---- C-P4: J -> B at depth (LTE continuum, 32 x 32 x 64) ---------------------------------------
+# ---- J -> B at depth (LTE continuum, 32 x 32 x 64) ---------------------------------------------
 def test_J_tends_to_B_at_depth():
     atm = make_atmosphere(0)
     dirs, w = s4_quadrature()
@@ -161,7 +161,7 @@ def test_J_tends_to_B_at_depth():
     assert r[tau > 1000].max() < r[(tau > 100) & (tau < 1000)].max()
 
 
-# ---- C-P6: octant symmetry --------------------------------------------------------------------
+# ---- octant symmetry --------------------------------------------------------------------------
 def test_mirror_symmetry_x():
     atm = make_atmosphere(1)
     nx, ny, nz = 16, 8, 24
@@ -186,7 +186,7 @@ def test_mirror_symmetry_x():
         np.testing.assert_allclose(a, b, rtol=1e-12, atol=0)
 
 
-# ---- C-P7: brute force per-point recursion on a tiny grid ---------------------------------------
+# ---- brute force per-point recursion on a tiny grid ---------------------------------------------
 def test_bruteforce_recursion_tiny():
     rng = np.random.default_rng(7)
     nx, ny, nz = 4, 3, 8
@@ -228,7 +228,7 @@ def test_bruteforce_recursion_tiny():
         np.testing.assert_allclose(I[d, 0].reshape(nz, ny, nx), ref, rtol=1e-12)
 
 
-# ---- C-P8: searchlight beam on the regular grid (Sect. 3.1) ------------------------------------
+# ---- searchlight beam on the regular grid (Sect. 3.1) ------------------------------------------
 def _searchlight_regular(periodic):
     n = 51
     h = 1.0 / (n - 1)

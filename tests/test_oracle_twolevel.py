@@ -1,4 +1,4 @@
-"""C-P5: the sqrt(epsilon) surface law of the two-level atom (Sect. 2.1, Eq. 3 and 4).
+"""The sqrt(epsilon) surface law of the two-level atom (Sect. 2.1, Eq. 3 and 4).
 
 For S = (1 - eps) J + eps B in an isothermal, semi-infinite, horizontally homogeneous medium the
 surface value is S(0) = sqrt(eps) B.  The oracle's regular-grid solver (nx = ny = 1, periodic, so
