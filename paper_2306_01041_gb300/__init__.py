@@ -7,6 +7,7 @@ Build the library first (``python -c "import __graft_entry__ as g; g.build()"`` 
 from ._lib import (RT_BC_ARRAY, RT_BC_THERMAL, RT_BC_ZERO, RT_SC_FACE,  # noqa: F401
                    RT_SC_PLANE, RTError, lib)
 from .api import (IDW, Atmos, Atom, Batch, EmergentIntensity, Grid, RegularGrid,  # noqa: F401
+                  SourceTerms,
                   VoronoiGrid, emergent_intensity, emergent_map, final_synthesis,
                   formal_solution,
                   formal_solution_adjoint,

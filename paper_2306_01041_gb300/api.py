@@ -460,6 +460,30 @@ class EmergentIntensity(torch.autograd.Function):
         return ga, gs, None, None, None, None
 
 
+class SourceTerms(torch.autograd.Function):
+    """(alpha, S) [nlam][npt] of the atom from the temperature T [npt] at fixed populations,
+    density and electron density (rt_source_terms); backward gives dL/dT from dL/dalpha and dL/dS
+    (rt_source_terms_adjoint).  Composed with EmergentIntensity it gives the gradient of an
+    emergent map with respect to T, alpha (the opacity) and S at every point."""
+
+    @staticmethod
+    def forward(ctx, T, grid, atom, atm, pops):
+        rho, ne, nH = atm.tensors[1:]
+        a = Atmos(T.detach().contiguous(), rho, ne, nH)
+        ctx.grid, ctx.atom, ctx.atm = grid, atom, a
+        ctx.save_for_backward(pops)
+        return source_terms(grid, atom, a, pops)
+
+    @staticmethod
+    def backward(ctx, g_alpha, g_S):
+        (pops,) = ctx.saved_tensors
+        ga = torch.zeros_like(pops[:1].expand(ctx.atom.nlam, -1)).contiguous() \
+            if g_alpha is None else g_alpha.contiguous()
+        gs = torch.zeros_like(ga) if g_S is None else g_S.contiguous()
+        gT = source_terms_adjoint(ctx.grid, ctx.atom, ctx.atm, pops, ga, gs)
+        return gT, None, None, None, None
+
+
 class Batch:
     """Several Voronoi grids solved by one persistent level-scheduled launch."""
 

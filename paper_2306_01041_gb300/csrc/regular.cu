@@ -179,11 +179,6 @@ rt_status regular_formal_solution(rt_grid *g, int nlam, const float *alpha, cons
 {
     if (nlam > 65535) return fail(RT_EINVAL, "nlam too large");
     if (g->sc_face) return face_formal_solution(g, nlam, alpha, S, bc, I_bc, J, I_dir, st);
-    if (!I_dir) {
-        bool done = false;
-        RT_TRY(regular_cluster_sweep(g, nlam, alpha, S, bc, J, st, &done));
-        if (done) return RT_OK;
-    }
     const size_t np = (size_t)g->nx * g->ny;
     const size_t ndh = std::max(g->dir_up.size(), g->dir_dn.size());
     void *p;

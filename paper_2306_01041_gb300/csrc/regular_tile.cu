@@ -12,10 +12,9 @@
 // every per-direction constant (offset, bilinear weights, half path length, quadrature weight) is
 // an operand from the kernel's constant bank.
 //
-// Three schedules of the same items: sc_wave_kernel (default) runs the whole formal solution as
+// Two schedules of the same items: sc_wave_kernel (default) runs the whole formal solution as
 // one persistent launch ordered by a device counter and per-item completion flags;
-// sc_pipe_kernel (opt-in) is that schedule with the next item's staging in flight during the
-// current one; sc_tile_kernel launches once per plane step.
+// sc_tile_kernel launches once per plane step.
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
@@ -89,13 +88,19 @@ __device__ __forceinline__ void lin_weights_thick(float d, float &ex, float &w0,
 {
     ex = exp_neg(d);
     const float e0 = 1.0f - ex;
-    const float r = rcp_fast(d);
-    w1 = fmaf(-e0, r, 1.0f);
-    w0 = fmaf(e0, r, -ex);
+    const float q = __fmul_rn(e0, rcp_fast(d));
+    w1 = 1.0f - q;
+    w0 = q - ex;
 }
 
 // Per-point updates of one staged item for every direction.  THICK: every interval of the item
-// has d >= 0.1, so only the exact interval weights are evaluated.
+// has d >= 0.1, so only the exact interval weights are evaluated.  The thread's two points (tile
+// rows R and R + 1) share every per-direction coefficient, so their arithmetic runs as packed
+// FP32 pairs (component 0: row R, component 1: row R + 1), in the operation order of the scalar
+// forms: iu = c0 I00 + c1 I01 + c2 I10 + c3 I11 (a product, then fused multiply-adds), the same
+// for S and alpha, dtau = (alpha_up + alpha) hds, I = iu e^-d + w0 S_up + w1 S, J += w I.
+// The staged (S, alpha) element at (row q, x) holds (S(x, q), S(x, q + 1), alpha(x, q),
+// alpha(x, q + 1)): one 16-byte load gives a corner of both points for S and for alpha.
 template <int NDH, bool WAVE, bool THICK, bool PP>
 __device__ __forceinline__ void tile_updates(const TileArgs &a, const WaveSt *sts, const float *It,
                                              const float4 *SA, int tsz, const int (&slot)[TL_PPT],
@@ -104,6 +109,8 @@ __device__ __forceinline__ void tile_updates(const TileArgs &a, const WaveSt *st
                                              size_t mstride, float (&jacc)[TL_PPT])
 {
     const int ndh = NDH > 0 ? NDH : a.ndh;
+    const float2 Sk2 = make_float2(Sk[0], Sk[1]), ak2 = make_float2(ak[0], ak[1]);
+    float2 j2 = make_float2(jacc[0], jacc[1]);
 #pragma unroll
     for (int d = 0; d < (NDH > 0 ? NDH : TL_MAX_DH); ++d) {
         if (NDH == 0 && d >= ndh) break;
@@ -119,37 +126,77 @@ __device__ __forceinline__ void tile_updates(const TileArgs &a, const WaveSt *st
             hds = a.hds[d], wd = a.w[d], off = a.off[d];
         }
         const float *Id = It + d * tsz;
-        // the thread's two points are vertically adjacent: their corner rows overlap, so three
-        // rows of intensity corners and (S, alpha) pairs serve both
         const int o = slot[0] + off;
-        const float ic[3][2] = {{Id[o], Id[o + 1]},
-                                {Id[o + TL_PW], Id[o + TL_PW + 1]},
-                                {Id[o + 2 * TL_PW], Id[o + 2 * TL_PW + 1]}};
-        const float4 pc[3] = {SA[o], SA[o + TL_PW], SA[o + 2 * TL_PW]};   // (S, alpha) at x, x + 1
+        // three rows of intensity corners serve both points
+        const float i00 = Id[o], i01 = Id[o + 1];
+        const float i10 = Id[o + TL_PW], i11 = Id[o + TL_PW + 1];
+        const float i20 = Id[o + 2 * TL_PW], i21 = Id[o + 2 * TL_PW + 1];
+        float2 iu = mul2(f2(c0), make_float2(i00, i10));
+        iu = fma2(f2(c1), make_float2(i01, i11), iu);
+        iu = fma2(f2(c2), make_float2(i10, i20), iu);
+        iu = fma2(f2(c3), make_float2(i11, i21), iu);
+        const float4 pa = SA[o], pb = SA[o + 1], pc = SA[o + TL_PW], pd = SA[o + TL_PW + 1];
+        float2 su = mul2(f2(c0), make_float2(pa.x, pa.y));
+        su = fma2(f2(c1), make_float2(pb.x, pb.y), su);
+        su = fma2(f2(c2), make_float2(pc.x, pc.y), su);
+        su = fma2(f2(c3), make_float2(pd.x, pd.y), su);
+        float2 au = mul2(f2(c0), make_float2(pa.z, pa.w));
+        au = fma2(f2(c1), make_float2(pb.z, pb.w), au);
+        au = fma2(f2(c2), make_float2(pc.z, pc.w), au);
+        au = fma2(f2(c3), make_float2(pd.z, pd.w), au);
+        const float2 dt = mul2(add2(au, ak2), f2(hds));
+        float2 ex, w0, w1;
+        if (THICK) {
+            lin_weights_thick2(dt, ex, w0, w1);
+        } else {
+            lin_weights(dt.x, ex.x, w0.x, w1.x);
+            lin_weights(dt.y, ex.y, w0.y, w1.y);
+        }
+        float2 v = mul2(iu, ex);
+        v = fma2(w0, su, v);
+        v = fma2(w1, Sk2, v);
+        const float vv[2] = {v.x, v.y};
 #pragma unroll
         for (int m = 0; m < TL_PPT; ++m) {
-            const float iu = c0 * ic[m][0] + c1 * ic[m][1] + c2 * ic[m + 1][0] + c3 * ic[m + 1][1];
-            const float4 p0 = pc[m], p1 = pc[m + 1];
-            const float su = c0 * p0.x + c1 * p0.z + c2 * p1.x + c3 * p1.z;
-            const float au = c0 * p0.y + c1 * p0.w + c2 * p1.y + c3 * p1.w;
-            const float dt = (au + ak[m]) * hds;
-            float ex, w0, w1;
-            if (THICK) lin_weights_thick(dt, ex, w0, w1);
-            else lin_weights(dt, ex, w0, w1);
-            const float v = iu * ex + w0 * su + w1 * Sk[m];
             if (ok[m]) {
                 float *dst = In + d * dstride + m * mstride;
-                if (WAVE) __stcg(dst, v);
-                else *dst = v;
+                if (WAVE) __stcg(dst, vv[m]);
+                else *dst = vv[m];
             }
-            jacc[m] += wd * v;
         }
+        j2 = fma2(f2(wd), v, j2);
     }
+    jacc[0] = j2.x;
+    jacc[1] = j2.y;
 }
 
-// S and alpha of an item's upwind plane into the shared (S, alpha) pairs (slot x holds x and
-// x + 1), with halo; returns the smallest alpha this thread staged.  No dependency on other
-// items: the persistent kernel issues these loads while it waits for the upwind intensities.
+// S and alpha of an item's upwind plane into the shared (S, alpha) elements (row q, x) =
+// (S(x, q), S(x, q + 1), alpha(x, q), alpha(x, q + 1)) for the staged rows q = 0 .. ph - 2, with
+// halo (the last staged row is only ever read as the second row of an element); returns the
+// smallest alpha this thread staged.  No dependency on other items: the persistent kernel issues
+// these loads while it waits for the upwind intensities.
+__device__ __forceinline__ float stage_sa_row(const TileArgs &a, const float *Su, const float *Au,
+                                              int x0, int y0, int hy, int e, float4 *SA)
+{
+    const int q4 = TL_PW / 4;
+    const int r = e / q4, c4 = e % q4;
+    const int gy = wrapi(y0 - hy + r, a.ny, a.wrap1);
+    const int gy1 = wrapi(y0 - hy + r + 1, a.ny, a.wrap1);
+    const int gx = wrapi(x0 - TL_HXP + 4 * c4, a.nx, a.wrap1);
+    const size_t g = (size_t)gy * a.nx + gx, g1 = (size_t)gy1 * a.nx + gx;
+    const float4 s0 = __ldg(reinterpret_cast<const float4 *>(Su + g));
+    const float4 s1 = __ldg(reinterpret_cast<const float4 *>(Su + g1));
+    const float4 a0 = __ldg(reinterpret_cast<const float4 *>(Au + g));
+    const float4 a1 = __ldg(reinterpret_cast<const float4 *>(Au + g1));
+    float4 *sa = SA + r * TL_PW + 4 * c4;
+    sa[0] = make_float4(s0.x, s1.x, a0.x, a1.x);
+    sa[1] = make_float4(s0.y, s1.y, a0.y, a1.y);
+    sa[2] = make_float4(s0.z, s1.z, a0.z, a1.z);
+    sa[3] = make_float4(s0.w, s1.w, a0.w, a1.w);
+    return fminf(fminf(fminf(a0.x, a0.y), fminf(a0.z, a0.w)),
+                 fminf(fminf(a1.x, a1.y), fminf(a1.z, a1.w)));
+}
+
 template <int HY>
 __device__ __forceinline__ float tile_stage_sa(const TileArgs &a, const PlaneCtx &c, int l, int x0,
                                                int y0, float *smt, int ndh)
@@ -161,22 +208,8 @@ __device__ __forceinline__ float tile_stage_sa(const TileArgs &a, const PlaneCtx
     const float *Su = a.S + (size_t)l * npt + (size_t)c.ku * a.np;
     const float *Au = a.alpha + (size_t)l * npt + (size_t)c.ku * a.np;
     float amin = __int_as_float(0x7f800000);
-    for (int e = threadIdx.x; e < ph * q4; e += TL_THREADS) {
-        const int r = e / q4, c4 = e % q4;
-        const int gy = wrapi(y0 - hy + r, a.ny, a.wrap1);
-        const int gx = wrapi(x0 - TL_HXP + 4 * c4, a.nx, a.wrap1);
-        const int gx4 = wrapi(gx + 4, a.nx, true);
-        const size_t g = (size_t)gy * a.nx + gx, g4 = (size_t)gy * a.nx + gx4;
-        const float4 sv = __ldg(reinterpret_cast<const float4 *>(Su + g));
-        const float4 av = __ldg(reinterpret_cast<const float4 *>(Au + g));
-        const float s4 = __ldg(Su + g4), a4 = __ldg(Au + g4);
-        float4 *sa = SA + r * TL_PW + 4 * c4;
-        sa[0] = make_float4(sv.x, av.x, sv.y, av.y);
-        sa[1] = make_float4(sv.y, av.y, sv.z, av.z);
-        sa[2] = make_float4(sv.z, av.z, sv.w, av.w);
-        sa[3] = make_float4(sv.w, av.w, s4, a4);
-        amin = fminf(amin, fminf(fminf(av.x, av.y), fminf(av.z, av.w)));
-    }
+    for (int e = threadIdx.x; e < (ph - 1) * q4; e += TL_THREADS)
+        amin = fminf(amin, stage_sa_row(a, Su, Au, x0, y0, hy, e, SA));
     return amin;
 }
 
@@ -229,19 +262,7 @@ __device__ __forceinline__ void tile_item(const TileArgs &a, const PlaneCtx &c, 
         const int gy = wrapi(y0 - hy + r, a.ny, a.wrap1);
         const int gx = wrapi(x0 - TL_HXP + 4 * c4, a.nx, a.wrap1);
         const size_t g = (size_t)gy * a.nx + gx;
-        if (!SA_DONE) {
-            const int gx4 = wrapi(gx + 4, a.nx, true);
-            const size_t g4 = (size_t)gy * a.nx + gx4;
-            const float4 sv = __ldg(reinterpret_cast<const float4 *>(Su + g));
-            const float4 av = __ldg(reinterpret_cast<const float4 *>(Au + g));
-            const float s4 = __ldg(Su + g4), a4 = __ldg(Au + g4);
-            float4 *sa = SA + r * TL_PW + 4 * c4;
-            sa[0] = make_float4(sv.x, av.x, sv.y, av.y);
-            sa[1] = make_float4(sv.y, av.y, sv.z, av.z);
-            sa[2] = make_float4(sv.z, av.z, sv.w, av.w);
-            sa[3] = make_float4(sv.w, av.w, s4, a4);
-            amin = fminf(amin, fminf(fminf(av.x, av.y), fminf(av.z, av.w)));
-        }
+        if (!SA_DONE && r < ph - 1) amin = fminf(amin, stage_sa_row(a, Su, Au, x0, y0, hy, e, SA));
         const float *src0;
         size_t dstep;
         if (WAVE) {
@@ -577,19 +598,12 @@ static bool uniform_stencils(const rt_grid *g)
     return true;
 }
 
-static rt_status pipe_sweep(rt_grid *g, const WaveArgs &wv, int nlam, cudaStream_t st, bool *done);
-static bool pipe_geometry(const rt_grid *g, int hy);
-static size_t pipe_scratch(const rt_grid *g, int nlam, int hy);
-
 size_t regular_wave_scratch(const rt_grid *g, int nlam)
 {
     const size_t ntiles = (size_t)((g->nx + TL_W - 1) / TL_W) * ((g->ny + TL_H - 1) / TL_H);
     const size_t plane = (size_t)nlam * ntiles * 12 * TL_W * TL_H;   // tile-major ring slot
     const size_t nflags = 2 * (size_t)g->nz * nlam * ntiles;
-    size_t bytes = 4 * plane * sizeof(float) + (nflags + 64) * sizeof(int);
-    int hy;
-    if (tile_geometry(g, hy) && pipe_geometry(g, hy)) bytes = std::max(bytes, pipe_scratch(g, nlam, hy));
-    return bytes;
+    return 4 * plane * sizeof(float) + (nflags + 64) * sizeof(int);
 }
 
 rt_status regular_wave_prepare(rt_grid *g, cudaStream_t st)
@@ -677,8 +691,6 @@ static rt_status wave_sweep(rt_grid *g, TileArgs &base, int nlam, int bc, cudaSt
         lc = std::max(1, std::min(nlam, lc));
         w.t[0].lchunk = w.t[1].lchunk = lc;
     }
-    RT_TRY(pipe_sweep(g, w, nlam, st, done));
-    if (*done) return RT_OK;
     const size_t plane = (size_t)nlam * base.ntiles * 12 * TL_W * TL_H;
     const size_t nflags = 2 * (size_t)g->nz * nlam * base.ntiles;
     void *p;
@@ -714,497 +726,6 @@ static rt_status wave_sweep(rt_grid *g, TileArgs &base, int nlam, int bc, cudaSt
     note_launch();
     kern<<<per_sm * nsm, TL_THREADS, smem, st>>>(w);
     RT_CUDA(cudaGetLastError());
-    *done = true;
-    return RT_OK;
-}
-
-// ---- Pipelined persistent sweep ------------------------------------------------------------------
-//
-// The wavefront schedule of sc_wave_kernel with the staging of the next item overlapped with the
-// computation of the current one.  One block of 512 threads per SM holds two staging buffers.
-// The intensity ring is tile major with each tile's halo stored beside it,
-// [nlam][tile][12][PH][TL_PW], so the 12 upwind planes an item needs are one contiguous block:
-// a single cp.async.bulk (the TMA engine, completion counted on an mbarrier) brings it into
-// shared memory.  S and alpha of the upwind plane (caller's arrays, periodic wrap) arrive by
-// 16-byte cp.async and are interleaved into (S, alpha) pairs for x and x + 1 after landing.
-// Writers store each point into its own tile's region and, near a tile edge, into the halo of
-// the neighbouring tile(s).  Applies to planes whose sides are multiples of 32 (at least 64) and
-// stencils within HY <= 4 rows.
-//
-// Ordering: an item's intensities are requested only once its 3 x 3 neighbours of the previous
-// step are complete.  The request for the next item is attempted (without waiting) while the
-// current one is computed; if the neighbours are not complete yet, it is made after the current
-// item is published.  A block only ever waits for items that precede, in counter order, every
-// item it holds, so by induction on the smallest unfinished item the waits cannot deadlock.
-// All waits are bounded (ERR_TIMEOUT).
-constexpr int PL_THREADS = 512;
-
-struct PipeArgs {
-    TileArgs t[2];             // per hemisphere (uniform z: the stencils as in sc_wave_kernel)
-    const WaveSt *st;          // [nz][2][12] per-plane stencils (non-uniform z), else null
-    float *ring[2][2];         // [hemisphere][step parity] padded tile-major planes
-    int *queue;
-    int *done;                 // [2][nz][nlam][ntiles] completion flags
-    int bc, first_hemi;
-};
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p)
-{
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *m, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(m)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// bounded wait for phase `parity` of an mbarrier to complete
-__device__ __forceinline__ bool mbar_wait(uint64_t *m, uint32_t parity)
-{
-    for (int it = 0; it < (1 << 20); ++it)
-        if (mbar_try_wait(m, parity)) return true;
-    return false;
-}
-
-// one thread: announce `bytes` on the mbarrier and start the bulk copy global -> shared
-__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *m)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                 :: "r"(smem_addr(m)), "r"(bytes) : "memory");
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-        :: "r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(m)) : "memory");
-}
-
-__device__ __forceinline__ void cp_async16(void *dst, const void *src)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(smem_addr(dst)), "l"(src)
-                 : "memory");
-}
-
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
-
-// flag index of item (h, s, l, tile)
-__device__ __forceinline__ size_t flag_at(const TileArgs &a, int h, int s, int l, int tile)
-{
-    return ((size_t)(h * a.nz + s) * a.nlam + l) * a.ntiles + tile;
-}
-
-// lanes 0..8 of one warp: the 3 x 3 neighbour flags of item `it` at its previous step.
-// blocking = false: one look; true: bounded wait.  Returns the warp-wide "all complete".
-__device__ __forceinline__ bool deps_ready(const PipeArgs &w, const WaveItem &it, bool blocking)
-{
-    const TileArgs &a = w.t[0];
-    const int lane = threadIdx.x & 31;
-    bool ok = true;
-    if (lane < 9) {
-        const int tx = a.tiles_x, ty = a.ntiles / a.tiles_x;
-        const int tx0 = it.tile % tx, ty0 = it.tile / tx;
-        const int nx_ = (tx0 + lane % 3 - 1 + tx) % tx, ny_ = (ty0 + lane / 3 - 1 + ty) % ty;
-        const int *f = w.done + flag_at(a, it.h, it.s - 1, it.l, ny_ * tx + nx_);
-        if (blocking) {
-            ok = wait_flag(f, a.err);
-        } else {
-            int v;
-            asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
-            ok = v != 0;
-        }
-    }
-    return __all_sync(0xffffffffu, ok);
-}
-
-// S and alpha of item `it`'s upwind plane into raw[0] (S) and raw[TSZ] (alpha), and of its own
-// points into own[0] and own[TL_W * TL_H]: 16-byte copies
-template <int HY>
-__device__ __forceinline__ void stage_sa_async(const TileArgs &a, const WaveItem &it, float *raw,
-                                               float *own)
-{
-    constexpr int PH = TL_H + 2 * HY, TSZ = PH * TL_PW, Q4 = TL_PW / 4;
-    const bool up = it.h == 0;
-    const int k = up ? it.s : a.nz - 1 - it.s;
-    const int ku = up ? k - 1 : k + 1;
-    const size_t npt = (size_t)a.np * a.nz;
-    const float *Sl = a.S + (size_t)it.l * npt, *Al = a.alpha + (size_t)it.l * npt;
-    const float *Su = Sl + (size_t)ku * a.np, *Au = Al + (size_t)ku * a.np;
-    for (int e = threadIdx.x; e < PH * Q4; e += PL_THREADS) {
-        const int r = e / Q4, c4 = e % Q4;
-        const int gy = wrapi(it.y0 - HY + r, a.ny, true);
-        const int gx = wrapi(it.x0 - TL_HXP + 4 * c4, a.nx, true);
-        const size_t g = (size_t)gy * a.nx + gx;
-        cp_async16(raw + r * TL_PW + 4 * c4, Su + g);
-        cp_async16(raw + TSZ + r * TL_PW + 4 * c4, Au + g);
-    }
-    if (threadIdx.x < TL_H * TL_W / 4) {
-        const int r = threadIdx.x / (TL_W / 4), c4 = threadIdx.x % (TL_W / 4);
-        const size_t g = (size_t)k * a.np + (size_t)(it.y0 + r) * a.nx + it.x0 + 4 * c4;
-        cp_async16(own + r * TL_W + 4 * c4, Sl + g);
-        cp_async16(own + TL_W * TL_H + r * TL_W + 4 * c4, Al + g);
-    }
-}
-
-// where a thread's point (row yl of the tile, column lx) is stored in the padded ring, as offsets
-// from the ring slot's wavelength base: its own tile's region and, near a tile edge, the halo of
-// the neighbouring tile(s); -1 where there is no such copy
-template <int HY>
-struct RingDst {
-    int own, xc, yc, cc;
-};
-
-template <int HY>
-__device__ __forceinline__ RingDst<HY> ring_dst(const TileArgs &a, int tile, int lx, int yl)
-{
-    constexpr int PH = TL_H + 2 * HY, TSZ = PH * TL_PW, REG = 12 * TSZ;
-    const int tx = a.tiles_x, ty = a.ntiles / a.tiles_x;
-    const int tx0 = tile % tx, ty0 = tile / tx;
-    RingDst<HY> r;
-    r.own = tile * REG + (yl + HY) * TL_PW + lx + TL_HXP;
-    int ntx = -1, col = 0, nty = -1, row = 0;
-    if (lx < TL_HXP) ntx = (tx0 + tx - 1) % tx, col = lx + TL_W + TL_HXP;
-    else if (lx >= TL_W - TL_HXP) ntx = (tx0 + 1) % tx, col = lx - (TL_W - TL_HXP);
-    if (yl < HY) nty = (ty0 + ty - 1) % ty, row = yl + TL_H + HY;
-    else if (yl >= TL_H - HY) nty = (ty0 + 1) % ty, row = yl - (TL_H - HY);
-    r.xc = ntx >= 0 ? (ty0 * tx + ntx) * REG + (yl + HY) * TL_PW + col : -1;
-    r.yc = nty >= 0 ? (nty * tx + tx0) * REG + row * TL_PW + lx + TL_HXP : -1;
-    r.cc = (ntx >= 0 && nty >= 0) ? (nty * tx + ntx) * REG + row * TL_PW + col : -1;
-    return r;
-}
-
-template <int HY>
-__device__ __forceinline__ void ring_store(float *base, const RingDst<HY> &r, int d, float v)
-{
-    constexpr int TSZ = (TL_H + 2 * HY) * TL_PW;
-    __stcg(base + r.own + d * TSZ, v);
-    if (r.xc >= 0) __stcg(base + r.xc + d * TSZ, v);
-    if (r.yc >= 0) {
-        __stcg(base + r.yc + d * TSZ, v);
-        if (r.cc >= 0) __stcg(base + r.cc + d * TSZ, v);
-    }
-}
-
-template <int HY, bool PP>
-__global__ void __launch_bounds__(PL_THREADS, 1) sc_pipe_kernel(PipeArgs w)
-{
-    constexpr int PH = TL_H + 2 * HY, TSZ = PH * TL_PW, REG = 12 * TSZ, NP = TL_W * TL_H;
-    extern __shared__ __align__(128) float smp[];
-    float *It = smp;                                             // [2][12][TSZ]
-    float *raw = smp + 2 * REG;                                  // [2][2][TSZ] upwind (S, alpha)
-    float *own = raw + 4 * TSZ;                                  // [2][2][NP] own plane (S, alpha)
-    float4 *SA = reinterpret_cast<float4 *>(own + 4 * NP);       // [TSZ]
-    __shared__ __align__(8) uint64_t mbar[2];
-    __shared__ WaveItem cur_s, nxt_s;
-    __shared__ int pf_s[2];   // [b]: the next item's intensities were requested during item b
-    __shared__ __align__(16) WaveSt sts[PP ? 12 : 1];
-    const TileArgs &a0 = w.t[0];
-    const int nt = a0.ntiles, nl = a0.nlam, nz = a0.nz;
-    const int total = 2 * nz * nl * nt;
-    const int tid = threadIdx.x, lx = tid % TL_W, ly = tid / TL_W;
-    const size_t npt = (size_t)a0.np * nz;
-
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&mbar[0])) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&mbar[1])) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        cur_s = wave_decode(a0, atomicAdd(w.queue, 1));
-        nxt_s = wave_decode(a0, atomicAdd(w.queue, 1));
-        pf_s[0] = pf_s[1] = 0;
-    }
-    __syncthreads();
-    uint32_t phase0 = 0, phase1 = 0;
-    int b = 0;
-    {
-        // the first item: wait for its neighbours (nothing else is held), then request it
-        const WaveItem c0 = cur_s;
-        if (c0.item >= total) return;
-        if (c0.s > 0) {
-            if (tid < 32) {
-                const bool ok = deps_ready(w, c0, true);
-                if (tid == 0) {
-                    if (!ok) flag_error(a0.err, ERR_TIMEOUT);
-                    asm volatile("fence.proxy.async.global;" ::: "memory");
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    bulk_load(It, w.ring[c0.h][(c0.s + 1) & 1] + ((size_t)c0.l * nt + c0.tile) * REG,
-                              REG * sizeof(float), &mbar[0]);
-                }
-            }
-            stage_sa_async<HY>(a0, c0, raw, own);
-        }
-        cp_async_commit();
-    }
-    for (;;) {
-        // cur_s and nxt_s were written before the barrier that ended the previous item
-        const WaveItem cur = cur_s, nxt = nxt_s;
-        if (cur.item >= total) break;
-        int claim = 0;
-        if (tid == 0) {
-            claim = atomicAdd(w.queue, 1);
-            pf_s[b] = 0;
-        }
-        const bool nxt_valid = nxt.item < total;
-        float *It_c = It + b * REG, *raw_c = raw + b * 2 * TSZ, *own_c = own + b * 2 * NP;
-        float *It_n = It + (b ^ 1) * REG;
-        // 1. S and alpha of the next item (inputs: no dependency)
-        if (nxt_valid && nxt.s > 0) stage_sa_async<HY>(a0, nxt, raw + (b ^ 1) * 2 * TSZ,
-                                                       own + (b ^ 1) * 2 * NP);
-        cp_async_commit();
-        // 2. the current item's staged data
-        bool lost = false;
-        if (cur.s > 0) {
-            lost = !mbar_wait(&mbar[b], b ? phase1 : phase0);
-            if (b) phase1 ^= 1u;
-            else phase0 ^= 1u;
-        }
-        cp_async_wait<1>();
-        if (__syncthreads_or(lost)) {
-            // the bulk copy did not complete: record it, give any copy still in flight a bounded
-            // time to land, and leave
-            if (tid == 0) {
-                flag_error(a0.err, ERR_TIMEOUT);
-                if (pf_s[b ^ 1]) mbar_wait(&mbar[b ^ 1], b ? phase0 : phase1);
-            }
-            cp_async_wait<0>();
-            return;
-        }
-        const bool up = cur.h == 0;
-        const int k = up ? cur.s : nz - 1 - cur.s;
-        const TileArgs &a = w.t[cur.h];
-        // 3. the consumed ring region is dead: drop it from L2 without a write-back; (S, alpha)
-        //    pairs; the thick-item vote; per-plane stencils; the J dependency; an attempt to
-        //    request the next item's intensities
-        float amin = __int_as_float(0x7f800000);
-        if (cur.s > 0) {
-            {   // REG floats = REG / 32 lines of 128 bytes (the region starts on a line)
-                const float *src = w.ring[cur.h][(cur.s + 1) & 1] + ((size_t)cur.l * nt + cur.tile) * REG;
-                for (int q = tid; q < REG / 32; q += PL_THREADS)
-                    asm volatile("discard.global.L2 [%0], 128;" :: "l"(src + q * 32) : "memory");
-            }
-            for (int e = tid; e < TSZ; e += PL_THREADS) {
-                const int c = e % TL_PW;
-                const float s0 = raw_c[e], a0v = raw_c[TSZ + e];
-                const float s1 = c + 1 < TL_PW ? raw_c[e + 1] : s0;
-                const float a1 = c + 1 < TL_PW ? raw_c[TSZ + e + 1] : a0v;
-                SA[e] = make_float4(s0, a0v, s1, a1);
-                amin = fminf(amin, a0v);
-            }
-            if (PP && tid < 12 * 8)
-                reinterpret_cast<int *>(sts)[tid] = __ldg(
-                    reinterpret_cast<const int *>(w.st + ((size_t)k * 2 + cur.h) * 12) + tid);
-        }
-        const bool first = cur.h == w.first_hemi;
-        if (tid < 32) {
-            if (!first) {   // the upward J of this plane and tile is complete
-                bool ok = true;
-                if (tid == 0) ok = wait_flag(w.done + flag_at(a0, 0, k, cur.l, cur.tile), a0.err);
-                ok = __shfl_sync(0xffffffffu, ok, 0);
-                if (tid == 0 && !ok) flag_error(a0.err, ERR_TIMEOUT);
-            }
-            if (nxt_valid && nxt.s > 0 && deps_ready(w, nxt, false)) {
-                if (tid == 0) {
-                    asm volatile("fence.proxy.async.global;" ::: "memory");
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    bulk_load(It_n, w.ring[nxt.h][(nxt.s + 1) & 1] +
-                                        ((size_t)nxt.l * nt + nxt.tile) * REG,
-                              REG * sizeof(float), &mbar[b ^ 1]);
-                    pf_s[b] = 1;
-                }
-            }
-        }
-        const float hds_min = PP ? (cur.s > 0 ? __ldg(&w.st[((size_t)k * 2 + cur.h) * 12].hds_min) : 0.f)
-                                 : a.hds_min;
-        const bool thick = __syncthreads_and(cur.s > 0 && amin * hds_min >= 0.1f * 1.0001f);
-        // 4. the item
-        float *ringn = w.ring[cur.h][cur.s & 1] + (size_t)cur.l * nt * REG;
-        float jacc[TL_PPT], jold[TL_PPT];
-        int gxy[TL_PPT];
-        RingDst<HY> dst[TL_PPT];
-#pragma unroll
-        for (int m = 0; m < TL_PPT; ++m) {
-            const int yl = ly + TL_ROWS * m;
-            gxy[m] = (cur.y0 + yl) * a0.nx + cur.x0 + lx;
-            dst[m] = ring_dst<HY>(a0, cur.tile, lx, yl);
-            jacc[m] = 0.f;
-            jold[m] = first ? 0.f : __ldcg(a0.J + (size_t)cur.l * npt + (size_t)k * a0.np + gxy[m]);
-        }
-        if (cur.s == 0) {
-            const float *Sl = a0.S + (size_t)cur.l * npt + (size_t)k * a0.np;
-#pragma unroll
-            for (int m = 0; m < TL_PPT; ++m) {
-                const float Sk = __ldg(Sl + gxy[m]);
-                const float v = (w.bc == RT_BC_THERMAL && up) ? Sk : 0.f;
-#pragma unroll
-                for (int d = 0; d < 12; ++d) {
-                    ring_store<HY>(ringn, dst[m], d, v);
-                    jacc[m] += a.w[d] * v;
-                }
-            }
-        } else {
-            float Sk[TL_PPT], ak[TL_PPT];
-            int slot[TL_PPT];
-#pragma unroll
-            for (int m = 0; m < TL_PPT; ++m) {
-                const int q = (ly + TL_ROWS * m) * TL_W + lx;
-                Sk[m] = own_c[q];
-                ak[m] = own_c[NP + q];
-                slot[m] = (ly + TL_ROWS * m + HY) * TL_PW + lx + TL_HXP;
-            }
-            auto body = [&](auto thick_tag) {
-                constexpr bool THICK = decltype(thick_tag)::value;
-#pragma unroll
-                for (int d = 0; d < 12; ++d) {
-                    float c0, c1, c2, c3, hds, wd;
-                    int off;
-                    if (PP) {
-                        const float4 q0 = reinterpret_cast<const float4 *>(sts)[2 * d];
-                        const float4 q1 = reinterpret_cast<const float4 *>(sts)[2 * d + 1];
-                        c0 = q0.x, c1 = q0.y, c2 = q0.z, c3 = q0.w;
-                        hds = q1.x, wd = q1.y, off = __float_as_int(q1.z);
-                    } else {
-                        c0 = a.cw[d][0], c1 = a.cw[d][1], c2 = a.cw[d][2], c3 = a.cw[d][3];
-                        hds = a.hds[d], wd = a.w[d], off = a.off[d];
-                    }
-                    const float *Id = It_c + d * TSZ;
-#pragma unroll
-                    for (int m = 0; m < TL_PPT; ++m) {
-                        const int o = slot[m] + off;
-                        const float iu = c0 * Id[o] + c1 * Id[o + 1] + c2 * Id[o + TL_PW] +
-                                         c3 * Id[o + TL_PW + 1];
-                        const float4 p0 = SA[o], p1 = SA[o + TL_PW];
-                        const float su = c0 * p0.x + c1 * p0.z + c2 * p1.x + c3 * p1.z;
-                        const float au = c0 * p0.y + c1 * p0.w + c2 * p1.y + c3 * p1.w;
-                        const float dt = (au + ak[m]) * hds;
-                        float ex, w0, w1;
-                        if (THICK) lin_weights_thick(dt, ex, w0, w1);
-                        else lin_weights(dt, ex, w0, w1);
-                        const float v = iu * ex + w0 * su + w1 * Sk[m];
-                        ring_store<HY>(ringn, dst[m], d, v);
-                        jacc[m] += wd * v;
-                    }
-                }
-            };
-            if (thick) body(std::true_type{});
-            else body(std::false_type{});
-        }
-#pragma unroll
-        for (int m = 0; m < TL_PPT; ++m) {
-            float *Jp = a0.J + (size_t)cur.l * npt + (size_t)k * a0.np + gxy[m];
-            const float v = first ? jacc[m] : jold[m] + jacc[m];
-            if (!isfinite(v)) flag_error(a0.err, ERR_NAN);
-            __stcg(Jp, v);
-        }
-        // the ring stores are read next by the bulk copies (async proxy) of other blocks
-        asm volatile("fence.proxy.async.global;" ::: "memory");
-        if (tid == 0) {   // every thread read cur_s and nxt_s before the first barrier of the item
-            cur_s = nxt;
-            nxt_s = wave_decode(a0, claim);
-        }
-        __syncthreads();
-        // 5. publish the item; request the next one now if the attempt above found it not ready
-        if (tid == 0) {
-            int *f = w.done + flag_at(a0, cur.h, cur.s, cur.l, cur.tile);
-            asm volatile("st.release.gpu.global.b32 [%0], %1;" :: "l"(f), "r"(1) : "memory");
-        }
-        if (tid < 32 && !pf_s[b] && nxt_valid && nxt.s > 0) {
-            const bool ok = deps_ready(w, nxt, true);
-            if (tid == 0) {
-                if (!ok) flag_error(a0.err, ERR_TIMEOUT);
-                asm volatile("fence.proxy.async.global;" ::: "memory");
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                bulk_load(It_n, w.ring[nxt.h][(nxt.s + 1) & 1] + ((size_t)nxt.l * nt + nxt.tile) * REG,
-                          REG * sizeof(float), &mbar[b ^ 1]);
-            }
-        }
-        b ^= 1;
-    }
-    cp_async_wait<0>();
-}
-
-// Scratch of the pipelined sweep: 4 padded ring slots, flags, counter.
-static size_t pipe_scratch(const rt_grid *g, int nlam, int hy)
-{
-    const size_t ntiles = (size_t)(g->nx / TL_W) * (g->ny / TL_H);
-    const size_t slot = (size_t)nlam * ntiles * 12 * (TL_H + 2 * hy) * TL_PW;
-    const size_t nflags = 2 * (size_t)g->nz * nlam * ntiles;
-    return 4 * slot * sizeof(float) + (nflags + 64) * sizeof(int);
-}
-
-static bool pipe_geometry(const rt_grid *g, int hy)
-{
-    return g->nx % TL_W == 0 && g->ny % TL_H == 0 && g->nx >= 2 * TL_W && g->ny >= 2 * TL_H &&
-           hy >= 1 && hy <= 4;
-}
-
-static bool pipe_applies(const rt_grid *g, int hy)
-{
-    const char *env = std::getenv("RT_REGULAR_SWEEP");   // opt-in: RT_REGULAR_SWEEP=pipe
-    return env && std::string(env) == "pipe" && pipe_geometry(g, hy);
-}
-
-template <int HY, bool PP>
-static rt_status launch_pipe(PipeArgs &w, cudaStream_t st)
-{
-    constexpr int PH = TL_H + 2 * HY, TSZ = PH * TL_PW;
-    const size_t smem = (size_t)(2 * 12 * TSZ + 4 * TSZ + 4 * TL_W * TL_H) * sizeof(float) +
-                        (size_t)TSZ * sizeof(float4);
-    RT_CUDA(cudaFuncSetAttribute(sc_pipe_kernel<HY, PP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem));
-    int per_sm = 0, dev = 0, nsm = 0;
-    RT_CUDA(cudaGetDevice(&dev));
-    RT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    RT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sc_pipe_kernel<HY, PP>, PL_THREADS,
-                                                          smem));
-    if (per_sm < 1) return fail(RT_ECAPACITY, "pipelined sweep cannot be resident");
-    note_launch();
-    sc_pipe_kernel<HY, PP><<<per_sm * nsm, PL_THREADS, smem, st>>>(w);
-    RT_CUDA(cudaGetLastError());
-    return RT_OK;
-}
-
-static rt_status pipe_sweep(rt_grid *g, const WaveArgs &wv, int nlam, cudaStream_t st, bool *done)
-{
-    const int hy = wv.t[0].hy;
-    if (!pipe_applies(g, hy)) return RT_OK;
-    const bool pp = wv.st != nullptr;
-    PipeArgs w;
-    w.t[0] = wv.t[0];
-    w.t[1] = wv.t[1];
-    w.st = wv.st;
-    w.bc = wv.bc;
-    w.first_hemi = wv.first_hemi;
-    const size_t ntiles = (size_t)wv.t[0].ntiles;
-    const size_t slot = (size_t)nlam * ntiles * 12 * (TL_H + 2 * hy) * TL_PW;
-    const size_t nflags = 2 * (size_t)g->nz * nlam * ntiles;
-    void *p;
-    RT_TRY(scratch_get(g, 3, pipe_scratch(g, nlam, hy), &p));
-    float *f = (float *)p;
-    w.ring[0][0] = f;
-    w.ring[0][1] = f + slot;
-    w.ring[1][0] = f + 2 * slot;
-    w.ring[1][1] = f + 3 * slot;
-    w.queue = (int *)(f + 4 * slot);
-    w.done = w.queue + 32;
-    RT_CUDA(cudaMemsetAsync(w.queue, 0, (nflags + 32) * sizeof(int), st));
-    rt_status r;
-    switch (hy * 2 + (pp ? 1 : 0)) {
-    case 2: r = launch_pipe<1, false>(w, st); break;
-    case 3: r = launch_pipe<1, true>(w, st); break;
-    case 4: r = launch_pipe<2, false>(w, st); break;
-    case 5: r = launch_pipe<2, true>(w, st); break;
-    case 6: r = launch_pipe<3, false>(w, st); break;
-    case 7: r = launch_pipe<3, true>(w, st); break;
-    case 8: r = launch_pipe<4, false>(w, st); break;
-    default: r = launch_pipe<4, true>(w, st); break;
-    }
-    RT_TRY(r);
     *done = true;
     return RT_OK;
 }

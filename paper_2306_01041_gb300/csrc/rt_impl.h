@@ -173,9 +173,6 @@ rt_status face_formal_solution(rt_grid *g, int nlam, const float *alpha, const f
 rt_status face_prepare(rt_grid *g, int nlam);
 // Voronoi tables: slot order, level offsets and upload from vt.h_up and vt.h_level
 rt_status voronoi_upload_slots(VorTables &vt, int64_t n, cudaStream_t st);
-// fused cluster sweep over all planes; *done = false when it does not apply to this grid
-rt_status regular_cluster_sweep(rt_grid *g, int nlam, const float *alpha, const float *S, int bc,
-                                float *J, cudaStream_t st, bool *done);
 // tiled per-plane sweep (default on periodic grids); *done = false when it does not apply
 rt_status regular_tile_sweep(rt_grid *g, int nlam, const float *alpha, const float *S, int bc,
                              float *J, float *buf0, float *buf1, cudaStream_t st, bool *done);
