@@ -324,8 +324,11 @@ rt_status rt_source_terms_lte_adjoint(int64_t npt, const float *T, const float *
 typedef struct rt_batch *rt_batch_t;
 
 /* A batch of Voronoi grids (same ndir) solved by one persistent level-scheduled launch.
- * lam_chunk[b] (host, may be NULL for the built-in choice) is the wavelength chunk each work
- * item of grid b carries; threads is the block size (0 = built-in). */
+ * lam_chunk[b] (host, may be NULL for the built-in chunk of 8) is the wavelength chunk each work
+ * item of grid b carries, rounded up to a multiple of 8 (a site's wavelengths are held in a row
+ * padded to whole chunks, a chunk filling whole 32-byte sectors) and to at most the block size; threads is the block size (0 = built-in; a multiple of 32 up to 512).  At most 128
+ * wavelengths.  Allocates the batch's fields: per grid 2 + ndir floats per (site, wavelength) of
+ * the padded rows. */
 rt_status rt_batch_create(const rt_grid_t *grids, int ngrids, int nlam, const int *lam_chunk,
                           int threads, rt_batch_t *out);
 void rt_batch_destroy(rt_batch_t batch);

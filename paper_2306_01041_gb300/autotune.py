@@ -59,7 +59,7 @@ def tune_batch(grids, alphas, Ss, nlam, candidates=None, reps=2, use_cache=True)
         return Batch(grids, nlam, lam_chunk=c["lam_chunk"], threads=c["threads"]), c
     nsm = torch.cuda.get_device_properties(0).multi_processor_count
     if candidates is None:
-        candidates = [(s, t) for t in (256, 512) for s in (0.25, 0.5, 1.0, 2.0)]
+        candidates = [(s, t) for t in (256, 512) for s in (0.0625, 0.125, 0.25, 0.5, 1.0)]
     best = None
     for scale, threads in candidates:
         lc = chunks_for(grids, nlam, scale, 4 * nsm)

@@ -7,8 +7,14 @@
 // formed by a reduction over the directions in index order (the same order and arithmetic as the
 // per-direction launches, so the results are identical).  No block ever waits for another: no
 // co-residency requirement and no device-side spin.  The grid is sized to the number of blocks
-// that fit at once (persistent) and items are queued largest first; chunk sizes per grid balance
-// the items' work (sites x chunk).
+// that fit at once (persistent) and items are queued largest first.
+//
+// Layout: site-major rows of P = nc cs wavelengths (the atom's, padded to whole chunks), cut into
+// chunks of cs (a multiple of 8) at offsets c cs: a chunk of a site fills whole 32-byte sectors,
+// so an upwind gather reads only the sectors it uses, and the items of the other chunks of the
+// same direction, which sweep the same sites at about the same time, read the same lines.
+// A thread keeps one wavelength lane (tid % cs) for a whole item and steps through the level's
+// sites, two at a time so that two independent gathers are in flight.
 #include <algorithm>
 #include <cmath>
 #include <numeric>
@@ -23,22 +29,21 @@ struct BatchGridDev {
     const int32_t *order;      // [ndir][n]
     const int64_t *lvl;        // level offsets, all directions concatenated
     const int32_t *lvl_base;   // [ndir + 1] start of each direction's offsets in lvl
-    const float2 *SA;          // [n][nlam] (S, alpha): the two are always gathered together
-    float *I;                  // [ndir][n][nlam] one intensity array per direction
-    float *J;                  // [n][nlam]
-    int n;
+    const float2 *SA;          // [n][P] (S, alpha): the two are always gathered together
+    float *I;                  // [ndir][n][P] one intensity array per direction
+    int n, cs, nc, P;          // P = nc cs
 };
 
-// Floats of one grid's field block: (S, alpha) pairs, J, one I per direction; rounded up to an
-// even count so that the next grid's pairs stay 8-byte aligned.
-static inline size_t batch_grid_floats(int64_t nsites, int nlam, int ndir)
+// Floats of one grid's field block (the pairs, one I per direction), rounded up to 64 floats so
+// that every grid's block starts on a 256-byte boundary.
+static inline size_t batch_grid_floats(int64_t nsites, int P, int ndir)
 {
-    const size_t m = (size_t)nsites * nlam;
-    return ((3 + (size_t)ndir) * m + 1) & ~(size_t)1;
+    const size_t m = (size_t)nsites * P;
+    return ((2 + (size_t)ndir) * m + 63) & ~(size_t)63;
 }
 
 struct BatchItem {
-    int grid, dir, c0, lc;
+    int grid, dir, chunk, lcv;   // lcv: valid wavelengths of the chunk (the last may be short)
 };
 
 struct BatchArgs {
@@ -51,24 +56,23 @@ struct BatchArgs {
     int nitems, ndir, nlam, bc;
 };
 
-// One (site, wavelength) update of a level, split into its loads (gather) and its arithmetic, so
-// that a thread can have the loads of one update in flight with the table loads of the next.
+// The loads of one (site, wavelength) update: the site's own (S, alpha) and, per upwind line, the
+// upwind intensity and (S, alpha).  c0 is the chunk's offset in a row (c cs) plus the lane.
 struct VorGather {
     float Si, Ai, I1, S1, A1, I2, S2, A2;
 };
 
 __device__ __forceinline__ VorGather vor_gather(const BatchGridDev &g, const float *I, const Upwind &u,
-                                                int i, int l, int nlam, float inflow_scale)
+                                                int i, size_t c0, int P, float inflow_scale)
 {
     VorGather r;
-    const size_t il = (size_t)i * nlam + l;
-    const float2 own = __ldg(g.SA + il);
+    const float2 own = __ldg(g.SA + c0 + (size_t)i * P);
     r.Si = own.x;
     r.Ai = own.y;
     // a wall neighbour (k < 0) takes the site's own S and alpha; -1 (inflow wall of the sweep)
     // brings the boundary intensity S * inflow_scale (1 thermal, 0 otherwise), -2 zero
     if (u.k1 >= 0) {
-        const size_t kl = (size_t)u.k1 * nlam + l;
+        const size_t kl = c0 + (size_t)u.k1 * P;
         r.I1 = I[kl];
         const float2 sa = __ldg(g.SA + kl);
         r.S1 = sa.x;
@@ -79,7 +83,7 @@ __device__ __forceinline__ VorGather vor_gather(const BatchGridDev &g, const flo
         r.I1 = u.k1 == -1 ? r.Si * inflow_scale : 0.f;
     }
     if (u.k2 >= 0 && u.w1 != 1.f) {
-        const size_t kl = (size_t)u.k2 * nlam + l;
+        const size_t kl = c0 + (size_t)u.k2 * P;
         r.I2 = I[kl];
         const float2 sa = __ldg(g.SA + kl);
         r.S2 = sa.x;
@@ -119,112 +123,91 @@ __global__ void __launch_bounds__(512, 2) batch_sweep_kernel(const BatchArgs a)
         if (it >= a.nitems) return;
         const BatchItem item = a.items[it];
         const BatchGridDev g = a.grids[item.grid];
-        const int d = item.dir;
+        const int d = item.dir, cs = g.cs;
         const Upwind *up = g.up + (size_t)d * g.n;
         const int32_t *order = g.order + (size_t)d * g.n;
-        float *I = g.I + (size_t)d * g.n * a.nlam;
+        float *I = g.I + (size_t)d * g.n * g.P;
         const int b0 = g.lvl_base[d], b1 = g.lvl_base[d + 1];
         const float inflow = (a.bc == RT_BC_THERMAL && a.up_flag[d] > 0.f) ? 1.f : 0.f;
-        const int lc = item.lc;
-        const int64_t B = blockDim.x;
+        // this thread's wavelength lane and first slot offset, fixed for the item; the threads
+        // beyond the last whole group of cs lanes, and the lanes past the chunk's end, sit out
+        const int step = blockDim.x / cs;
+        const int j = threadIdx.x % cs, soff = threadIdx.x / cs;
+        const bool active = soff < step && j < item.lcv;
+        const size_t c0 = (size_t)item.chunk * cs + j;
+        const int P = g.P;
         for (int L = b0; L + 1 < b1; ++L) {
-            const int64_t s0 = g.lvl[L], s1 = g.lvl[L + 1];
-            const int64_t work = (s1 - s0) * lc;
-            // the tables (upwind record, site) of a thread's next update are loaded before the
-            // gathers of the current one: two independent load streams in flight per thread
-            auto table = [&](int64_t t, Upwind &uu, int &ii, int &ll) {
-                const int64_t slot = s0 + t / lc;
-                ll = item.c0 + (int)(t % lc);
-                uu = up[slot];
-                ii = order[slot];
-            };
-            int64_t t = threadIdx.x;
-            Upwind u;
-            int i = 0, l = 0;
-            if (t < work) table(t, u, i, l);
-            while (t < work) {
-                const int64_t tn = t + B;
-                Upwind un;
-                int in = 0, ln = 0;
-                if (tn < work) table(tn, un, in, ln);
-                const VorGather gr = vor_gather(g, I, u, i, l, a.nlam, inflow);
-                I[(size_t)i * a.nlam + l] = vor_update(u, gr);
-                t = tn;
-                u = un;
-                i = in;
-                l = ln;
+            const int64_t s1 = g.lvl[L + 1];
+            if (active) {
+                for (int64_t sa = g.lvl[L] + soff; sa < s1; sa += 2 * step) {
+                    const int64_t sb = sa + step;
+                    const bool two = sb < s1;
+                    const Upwind ua = up[sa];
+                    const int ia = order[sa];
+                    Upwind ub = ua;
+                    int ib = ia;
+                    if (two) {
+                        ub = up[sb];
+                        ib = order[sb];
+                    }
+                    const VorGather ga = vor_gather(g, I, ua, ia, c0, P, inflow);
+                    VorGather gb = ga;
+                    if (two) gb = vor_gather(g, I, ub, ib, c0, P, inflow);
+                    I[c0 + (size_t)ia * P] = vor_update(ua, ga);
+                    if (two) I[c0 + (size_t)ib * P] = vor_update(ub, gb);
+                }
             }
             __syncthreads();
         }
     }
 }
 
-// J[i][l] = sum_d w_d I_d[i][l], directions in index order
-__global__ void batch_reduce_kernel(const float *I, float *J, const float *wdir, int ndir,
-                                    size_t m, unsigned *err)
+// J[l][i] = sum_d w_d I_d, directions in index order, for 32 sites per block: the sums are formed
+// along the sites' rows (coalesced reads) and written wavelength-major through a shared tile.
+__global__ void batch_reduce_kernel(const float *__restrict__ I, float *__restrict__ J,
+                                    const float *__restrict__ wdir, int ndir, int n, int P,
+                                    int nlam, unsigned *err)
 {
-    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= m) return;
-    float acc = wdir[0] * I[t];
-    for (int d = 1; d < ndir; ++d) acc = acc + wdir[d] * I[(size_t)d * m + t];
-    if (!isfinite(acc)) flag_error(err, ERR_NAN);
-    J[t] = acc;
-}
-
-__global__ void transpose_kernel_b(const float *__restrict__ in, float *__restrict__ out, int rows,
-                                   int cols)
-{
-    __shared__ float tile[32][33];
-    int c = blockIdx.x * 32 + threadIdx.x;
-    int r0 = blockIdx.y * 32;
-    for (int dr = threadIdx.y; dr < 32; dr += blockDim.y) {
-        int r = r0 + dr;
-        if (r < rows && c < cols) tile[dr][threadIdx.x] = in[(size_t)r * cols + c];
+    __shared__ float tile[128][33];
+    const int i0 = blockIdx.x * 32;
+    const size_t dstride = (size_t)n * P;
+    for (int e = threadIdx.x; e < 32 * P; e += blockDim.x) {
+        const int il = e / P, l = e % P, i = i0 + il;
+        if (i >= n || l >= nlam) continue;
+        const size_t q = (size_t)i * P + l;
+        float acc = wdir[0] * I[q];
+        for (int d = 1; d < ndir; ++d) acc = acc + wdir[d] * I[(size_t)d * dstride + q];
+        if (!isfinite(acc)) flag_error(err, ERR_NAN);
+        tile[l][il] = acc;
     }
     __syncthreads();
-    int r = r0 + threadIdx.x;
-    for (int dc = threadIdx.y; dc < 32; dc += blockDim.y) {
-        int cc = blockIdx.x * 32 + dc;
-        if (r < rows && cc < cols) out[(size_t)cc * rows + r] = tile[threadIdx.x][dc];
+    for (int e = threadIdx.x; e < 32 * nlam; e += blockDim.x) {
+        const int l = e / 32, il = e % 32, i = i0 + il;
+        if (i < n) J[(size_t)l * n + i] = tile[l][il];
     }
 }
 
-static void transpose_b(const float *in, float *out, int rows, int cols, cudaStream_t st)
+// S, alpha [nlam][n] -> the (S, alpha) rows [n][P], 32 sites per block; the padding lanes are zero
+// (never read).
+__global__ void batch_pack_kernel(const float *__restrict__ S, const float *__restrict__ A,
+                                  float2 *__restrict__ SA, int n, int P, int nlam)
 {
-    dim3 grid((cols + 31) / 32, (rows + 31) / 32);
-    note_launch();
-    transpose_kernel_b<<<grid, dim3(32, 8), 0, st>>>(in, out, rows, cols);
-}
-
-// S, alpha [rows][cols] -> (S, alpha) pairs [cols][rows]
-__global__ void transpose_pair_kernel(const float *__restrict__ S, const float *__restrict__ A,
-                                      float2 *__restrict__ out, int rows, int cols)
-{
-    __shared__ float ts[32][33], ta[32][33];
-    int c = blockIdx.x * 32 + threadIdx.x;
-    int r0 = blockIdx.y * 32;
-    for (int dr = threadIdx.y; dr < 32; dr += blockDim.y) {
-        int r = r0 + dr;
-        if (r < rows && c < cols) {
-            ts[dr][threadIdx.x] = S[(size_t)r * cols + c];
-            ta[dr][threadIdx.x] = A[(size_t)r * cols + c];
+    __shared__ float ts[128][33], ta[128][33];
+    const int i0 = blockIdx.x * 32;
+    for (int e = threadIdx.x; e < 32 * nlam; e += blockDim.x) {
+        const int l = e / 32, il = e % 32, i = i0 + il;
+        if (i < n) {
+            const size_t q = (size_t)l * n + i;
+            ts[l][il] = S[q];
+            ta[l][il] = A[q];
         }
     }
     __syncthreads();
-    int r = r0 + threadIdx.x;
-    for (int dc = threadIdx.y; dc < 32; dc += blockDim.y) {
-        int cc = blockIdx.x * 32 + dc;
-        if (r < rows && cc < cols)
-            out[(size_t)cc * rows + r] = make_float2(ts[threadIdx.x][dc], ta[threadIdx.x][dc]);
+    for (int e = threadIdx.x; e < 32 * P; e += blockDim.x) {
+        const int il = e / P, l = e % P, i = i0 + il;
+        if (i >= n) continue;
+        SA[(size_t)i * P + l] = l < nlam ? make_float2(ts[l][il], ta[l][il]) : make_float2(0.f, 0.f);
     }
-}
-
-static void transpose_pair(const float *S, const float *A, float2 *out, int rows, int cols,
-                           cudaStream_t st)
-{
-    dim3 grid((cols + 31) / 32, (rows + 31) / 32);
-    note_launch();
-    transpose_pair_kernel<<<grid, dim3(32, 8), 0, st>>>(S, A, out, rows, cols);
 }
 
 }  // namespace rt
@@ -241,7 +224,7 @@ struct rt_batch {
     int64_t *d_lvl = nullptr;
     int32_t *d_lvl_base = nullptr;
     float *d_wdir = nullptr, *d_upf = nullptr;
-    float *d_fields = nullptr;   // per grid A, S, J [n][nlam] and I [ndir][n][nlam]
+    float *d_fields = nullptr;   // per grid (S, alpha) [n][P] and I [ndir][n][P]
     int *d_queue = nullptr;
     unsigned *d_err = nullptr;
     unsigned *err = nullptr;     // where kernels flag errors: d_err, or the grid's for a batch of one
@@ -297,7 +280,7 @@ rt_status rt_batch_create(const rt_grid_t *grids, int ngrids, int nlam, const in
             delete b;
             return fail(RT_EINVAL, "threads must be a multiple of 32 up to 512");
         }
-        int64_t ntot = 0, nmin = INT64_MAX;
+
         for (int i = 0; i < ngrids; ++i) {
             rt_grid *g = grids[i];
             if (!g || g->kind != RT_GRID_VORONOI || g->ndir != b->ndir) {
@@ -310,8 +293,6 @@ rt_status rt_batch_create(const rt_grid_t *grids, int ngrids, int nlam, const in
                     return fail(RT_EINVAL, "batch grids must share the quadrature");
                 }
             b->grids.push_back(g);
-            ntot += g->nsites;
-            nmin = std::min<int64_t>(nmin, g->nsites);
         }
         int dev = 0, nsm = 0, per_sm = 0;
         RT_CUDA(cudaGetDevice(&dev));
@@ -322,23 +303,27 @@ rt_status rt_batch_create(const rt_grid_t *grids, int ngrids, int nlam, const in
             return fail(RT_ECAPACITY, "the batched sweep kernel cannot be resident");
         }
         b->blocks = nsm * per_sm;
-        // items: default chunk sizes make every item carry about the same number of (site, lambda,
-        // direction) updates, about total / (2 * resident blocks)
+        if (nlam > 128) {
+            delete b;
+            return fail(RT_EINVAL, "the batched sweep takes at most 128 wavelengths");
+        }
+        // chunks: the requested wavelength count per item, rounded up to a multiple of 8 floats
+        // (the chunk stride cs): a chunk of a site fills whole 32-byte sectors.  Default 8: the
+        // smallest sector-exact chunk gives the most items (the parallelism of the launch) and
+        // measured fastest both for one grid and for the 8-atmosphere batch.
+        const int nlam8 = (nlam + 7) & ~7;
+        std::vector<int> cs(ngrids), nc(ngrids);
         for (int i = 0; i < ngrids; ++i) {
-            int lc;
-            if (lam_chunk) {
-                lc = lam_chunk[i];
-            } else {
-                const double target = (double)ntot * nlam * b->ndir / (2.0 * b->blocks);
-                lc = (int)std::lround(target / (double)grids[i]->nsites);
-            }
+            int lc = lam_chunk ? lam_chunk[i] : 8;
             lc = std::max(1, std::min(nlam, lc));
+            cs[i] = std::min(std::min(nlam8, (lc + 7) & ~7), b->threads & ~7);
+            nc[i] = (nlam + cs[i] - 1) / cs[i];
             for (int d = 0; d < b->ndir; ++d)
-                for (int c0 = 0; c0 < nlam; c0 += lc)
-                    b->h_items.push_back(BatchItem{i, d, c0, std::min(lc, nlam - c0)});
+                for (int c = 0; c < nc[i]; ++c)
+                    b->h_items.push_back(BatchItem{i, d, c, std::min(cs[i], nlam - c * cs[i])});
         }
         std::stable_sort(b->h_items.begin(), b->h_items.end(), [&](const BatchItem &x, const BatchItem &y) {
-            return (double)grids[x.grid]->nsites * x.lc > (double)grids[y.grid]->nsites * y.lc;
+            return (double)grids[x.grid]->nsites * x.lcv > (double)grids[y.grid]->nsites * y.lcv;
         });
         // device tables
         std::vector<int64_t> lvl;
@@ -354,7 +339,11 @@ rt_status rt_batch_create(const rt_grid_t *grids, int ngrids, int nlam, const in
             base.push_back((int32_t)lvl.size());
         }
         size_t fsz = 0;
-        for (int i = 0; i < ngrids; ++i) fsz += batch_grid_floats(grids[i]->nsites, nlam, b->ndir);
+        std::vector<int> P(ngrids);
+        for (int i = 0; i < ngrids; ++i) {
+            P[i] = nc[i] * cs[i];
+            fsz += batch_grid_floats(grids[i]->nsites, P[i], b->ndir);
+        }
         std::vector<float> wd(b->ndir), uf(b->ndir);
         for (int d = 0; d < b->ndir; ++d) {
             wd[d] = (float)grids[0]->wdir[d];
@@ -381,17 +370,19 @@ rt_status rt_batch_create(const rt_grid_t *grids, int ngrids, int nlam, const in
         float *f = b->d_fields;
         for (int i = 0; i < ngrids; ++i) {
             rt_grid *g = grids[i];
-            const size_t m = (size_t)g->nsites * nlam;
+            const size_t m = (size_t)g->nsites * P[i];
             BatchGridDev gd;
             gd.up = g->vt.d_up;
             gd.order = g->vt.d_order;
             gd.lvl = b->d_lvl;
             gd.lvl_base = b->d_lvl_base + base_at[i];
             gd.SA = reinterpret_cast<const float2 *>(f);
-            gd.J = f + 2 * m;
-            gd.I = f + 3 * m;
+            gd.I = f + 2 * m;
             gd.n = (int)g->nsites;
-            f += batch_grid_floats(g->nsites, nlam, b->ndir);
+            gd.cs = cs[i];
+            gd.nc = nc[i];
+            gd.P = P[i];
+            f += batch_grid_floats(g->nsites, P[i], b->ndir);
             b->h_grids.push_back(gd);
         }
         BT(cudaMemcpy(b->d_items, b->h_items.data(), b->h_items.size() * sizeof(BatchItem),
@@ -427,7 +418,9 @@ rt_status rt_batch_formal_solution(rt_batch_t b, const float *const *alpha, cons
         for (int i = 0; i < ng; ++i) {
             if (!alpha[i] || !S[i] || !J[i]) return fail(RT_EINVAL, "null field");
             const BatchGridDev &g = b->h_grids[i];
-            transpose_pair(S[i], alpha[i], const_cast<float2 *>(g.SA), b->nlam, g.n, st);
+            note_launch();
+            batch_pack_kernel<<<(unsigned)((g.n + 31) / 32), 256, 0, st>>>(
+                S[i], alpha[i], const_cast<float2 *>(g.SA), g.n, g.P, b->nlam);
         }
         RT_CUDA(cudaMemsetAsync(b->d_queue, 0, sizeof(int), st));
         BatchArgs a;
@@ -446,11 +439,9 @@ rt_status rt_batch_formal_solution(rt_batch_t b, const float *const *alpha, cons
         batch_sweep_kernel<<<blocks, b->threads, 0, st>>>(a);
         for (int i = 0; i < ng; ++i) {
             const BatchGridDev &g = b->h_grids[i];
-            const size_t m = (size_t)g.n * b->nlam;
             note_launch();
-            batch_reduce_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(g.I, g.J, b->d_wdir,
-                                                                             b->ndir, m, b->err);
-            transpose_b(g.J, J[i], g.n, b->nlam, st);
+            batch_reduce_kernel<<<(unsigned)((g.n + 31) / 32), 256, 0, st>>>(
+                g.I, J[i], b->d_wdir, b->ndir, g.n, g.P, b->nlam, b->err);
         }
         RT_CUDA(cudaGetLastError());
         return RT_OK;

@@ -186,54 +186,62 @@ __global__ void __launch_bounds__(FACE_MAXW * 32, 1) face_sweep_kernel(FaceArgs 
                 if (r < 0) r += na;
                 return D.sa > 0 ? r : na - 1 - r;
             };
-            float pf[5][MAXM];
-            auto fetch = [&](int al) {
+            // a ring of PD lines in flight: the loads of a line are issued PD line steps before
+            // the line is computed (the loop is unrolled by PD so that every buffer is a fixed set
+            // of registers)
+            constexpr int PD = MAXM <= 4 ? 3 : 2;
+            float pf[PD][5][MAXM];
+            auto fetch = [&](float (&buf5)[5][MAXM], int al) {
 #pragma unroll
                 for (int q = 0; q < MAXM; ++q) {
                     const int b = lane + 32 * q;
                     if (q < M && b < nb) {
                         const size_t fk = lidx(k, al, b), fu = lidx(ku, al, b);
-                        pf[0][q] = __ldg(Sl + fk);
-                        pf[1][q] = __ldg(Al + fk);
-                        pf[2][q] = buf[(size_t)al * nb + b];
-                        pf[3][q] = __ldg(Sl + fu);
-                        pf[4][q] = __ldg(Al + fu);
+                        buf5[0][q] = __ldg(Sl + fk);
+                        buf5[1][q] = __ldg(Al + fk);
+                        buf5[2][q] = buf[(size_t)al * nb + b];
+                        buf5[3][q] = __ldg(Sl + fu);
+                        buf5[4][q] = __ldg(Al + fu);
                     }
                 }
             };
-            auto stash = [&](int slot) {
+            auto stash = [&](const float (&buf5)[5][MAXM], int slot) {
 #pragma unroll
                 for (int q = 0; q < MAXM; ++q) {
                     const int b = lane + 32 * q;
                     if (q < M && b < nb) {
-                        RING(R_SK, slot, b) = pf[0][q];
-                        RING(R_AK, slot, b) = pf[1][q];
-                        RING(R_IU, slot, b) = pf[2][q];
-                        RING(R_SU, slot, b) = pf[3][q];
-                        RING(R_AU, slot, b) = pf[4][q];
+                        RING(R_SK, slot, b) = buf5[0][q];
+                        RING(R_AK, slot, b) = buf5[1][q];
+                        RING(R_IU, slot, b) = buf5[2][q];
+                        RING(R_SU, slot, b) = buf5[3][q];
+                        RING(R_AU, slot, b) = buf5[4][q];
                     }
                 }
             };
             const float g1 = st.fb, g0 = 1.f - st.fb;
             int slot = 0;
-            int m = -st.warm - 1;
-            fetch(line_of(m));
-            stash(slot);
+            const int m0 = -st.warm;
+            fetch(pf[0], line_of(m0 - 1));
+            stash(pf[0], slot);
             // this plane's intensity on the line before the walk: the previous plane's as a start
             // (vertical face), unused on the plane face (wK = 0)
 #pragma unroll
             for (int q = 0; q < MAXM; ++q) {
                 const int b = lane + 32 * q;
-                if (q < M && b < nb) RING(R_IK, slot, b) = st.wK != 0.f ? pf[2][q] : 0.f;
+                if (q < M && b < nb) RING(R_IK, slot, b) = st.wK != 0.f ? pf[0][2][q] : 0.f;
             }
-            fetch(line_of(m + 1));
+#pragma unroll
+            for (int p = 0; p < PD; ++p)
+                if (m0 + p < na) fetch(pf[p], line_of(m0 + p));
             __syncwarp();
-            for (m = -st.warm; m < na; ++m) {
+            // one line step: stash the line's prefetched inputs, refill the buffer PD lines ahead,
+            // compute the line
+            auto step = [&](float (&buf5)[5][MAXM], int m) {
                 const int al = line_of(m);
                 slot ^= 1;
                 const int cur = slot, prv = slot ^ 1;
-                stash(cur);
-                if (m + 1 < na) fetch(line_of(m + 1));
+                stash(buf5, cur);
+                if (m + PD < na) fetch(buf5, line_of(m + PD));
                 __syncwarp();
                 const bool store = m >= 0;
 #pragma unroll
@@ -268,6 +276,11 @@ __global__ void __launch_bounds__(FACE_MAXW * 32, 1) face_sweep_kernel(FaceArgs 
                     }
                 }
                 __syncwarp();
+            };
+            for (int m = m0; m < na; m += PD) {
+#pragma unroll
+                for (int p = 0; p < PD; ++p)
+                    if (m + p < na) step(pf[p], m + p);
             }
         }
         __syncthreads();

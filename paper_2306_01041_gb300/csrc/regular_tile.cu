@@ -99,8 +99,8 @@ __device__ __forceinline__ void lin_weights_thick(float d, float &ex, float &w0,
 // FP32 pairs (component 0: row R, component 1: row R + 1), in the operation order of the scalar
 // forms: iu = c0 I00 + c1 I01 + c2 I10 + c3 I11 (a product, then fused multiply-adds), the same
 // for S and alpha, dtau = (alpha_up + alpha) hds, I = iu e^-d + w0 S_up + w1 S, J += w I.
-// The staged (S, alpha) element at (row q, x) holds (S(x, q), S(x, q + 1), alpha(x, q),
-// alpha(x, q + 1)): one 16-byte load gives a corner of both points for S and for alpha.
+// The staged (S, alpha) element at (row q, x) holds S and alpha at x and x + 1, so three 16-byte
+// loads (rows q .. q + 2) give every S and alpha corner of both points.
 template <int NDH, bool WAVE, bool THICK, bool PP>
 __device__ __forceinline__ void tile_updates(const TileArgs &a, const WaveSt *sts, const float *It,
                                              const float4 *SA, int tsz, const int (&slot)[TL_PPT],
@@ -135,15 +135,16 @@ __device__ __forceinline__ void tile_updates(const TileArgs &a, const WaveSt *st
         iu = fma2(f2(c1), make_float2(i01, i11), iu);
         iu = fma2(f2(c2), make_float2(i10, i20), iu);
         iu = fma2(f2(c3), make_float2(i11, i21), iu);
-        const float4 pa = SA[o], pb = SA[o + 1], pc = SA[o + TL_PW], pd = SA[o + TL_PW + 1];
-        float2 su = mul2(f2(c0), make_float2(pa.x, pa.y));
-        su = fma2(f2(c1), make_float2(pb.x, pb.y), su);
-        su = fma2(f2(c2), make_float2(pc.x, pc.y), su);
-        su = fma2(f2(c3), make_float2(pd.x, pd.y), su);
-        float2 au = mul2(f2(c0), make_float2(pa.z, pa.w));
-        au = fma2(f2(c1), make_float2(pb.z, pb.w), au);
-        au = fma2(f2(c2), make_float2(pc.z, pc.w), au);
-        au = fma2(f2(c3), make_float2(pd.z, pd.w), au);
+        // (S, alpha) at x and x + 1 of three rows: rows 0-1 serve the first point, 1-2 the second
+        const float4 p0 = SA[o], p1 = SA[o + TL_PW], p2 = SA[o + 2 * TL_PW];
+        float2 su = mul2(f2(c0), make_float2(p0.x, p1.x));
+        su = fma2(f2(c1), make_float2(p0.z, p1.z), su);
+        su = fma2(f2(c2), make_float2(p1.x, p2.x), su);
+        su = fma2(f2(c3), make_float2(p1.z, p2.z), su);
+        float2 au = mul2(f2(c0), make_float2(p0.y, p1.y));
+        au = fma2(f2(c1), make_float2(p0.w, p1.w), au);
+        au = fma2(f2(c2), make_float2(p1.y, p2.y), au);
+        au = fma2(f2(c3), make_float2(p1.w, p2.w), au);
         const float2 dt = mul2(add2(au, ak2), f2(hds));
         float2 ex, w0, w1;
         if (THICK) {
@@ -170,31 +171,30 @@ __device__ __forceinline__ void tile_updates(const TileArgs &a, const WaveSt *st
     jacc[1] = j2.y;
 }
 
-// S and alpha of an item's upwind plane into the shared (S, alpha) elements (row q, x) =
-// (S(x, q), S(x, q + 1), alpha(x, q), alpha(x, q + 1)) for the staged rows q = 0 .. ph - 2, with
-// halo (the last staged row is only ever read as the second row of an element); returns the
-// smallest alpha this thread staged.  No dependency on other items: the persistent kernel issues
-// these loads while it waits for the upwind intensities.
+// S and alpha of an item's upwind plane into the shared (S, alpha) pairs (slot x of row r holds
+// (S, alpha) at x and x + 1), with halo; element e covers four slots of row e / (TL_PW / 4) from
+// two 16-byte loads and two scalar ones.  A float4 never straddles the periodic seam because nx
+// and x0 - TL_HXP are multiples of 4.  Returns the smallest alpha this thread staged.  No
+// dependency on other items: the persistent kernel issues these loads while it waits for the
+// upwind intensities.
 __device__ __forceinline__ float stage_sa_row(const TileArgs &a, const float *Su, const float *Au,
                                               int x0, int y0, int hy, int e, float4 *SA)
 {
     const int q4 = TL_PW / 4;
     const int r = e / q4, c4 = e % q4;
     const int gy = wrapi(y0 - hy + r, a.ny, a.wrap1);
-    const int gy1 = wrapi(y0 - hy + r + 1, a.ny, a.wrap1);
     const int gx = wrapi(x0 - TL_HXP + 4 * c4, a.nx, a.wrap1);
-    const size_t g = (size_t)gy * a.nx + gx, g1 = (size_t)gy1 * a.nx + gx;
-    const float4 s0 = __ldg(reinterpret_cast<const float4 *>(Su + g));
-    const float4 s1 = __ldg(reinterpret_cast<const float4 *>(Su + g1));
-    const float4 a0 = __ldg(reinterpret_cast<const float4 *>(Au + g));
-    const float4 a1 = __ldg(reinterpret_cast<const float4 *>(Au + g1));
+    const int gx4 = wrapi(gx + 4, a.nx, true);
+    const size_t g = (size_t)gy * a.nx + gx, g4 = (size_t)gy * a.nx + gx4;
+    const float4 sv = __ldg(reinterpret_cast<const float4 *>(Su + g));
+    const float4 av = __ldg(reinterpret_cast<const float4 *>(Au + g));
+    const float s4 = __ldg(Su + g4), a4 = __ldg(Au + g4);
     float4 *sa = SA + r * TL_PW + 4 * c4;
-    sa[0] = make_float4(s0.x, s1.x, a0.x, a1.x);
-    sa[1] = make_float4(s0.y, s1.y, a0.y, a1.y);
-    sa[2] = make_float4(s0.z, s1.z, a0.z, a1.z);
-    sa[3] = make_float4(s0.w, s1.w, a0.w, a1.w);
-    return fminf(fminf(fminf(a0.x, a0.y), fminf(a0.z, a0.w)),
-                 fminf(fminf(a1.x, a1.y), fminf(a1.z, a1.w)));
+    sa[0] = make_float4(sv.x, av.x, sv.y, av.y);
+    sa[1] = make_float4(sv.y, av.y, sv.z, av.z);
+    sa[2] = make_float4(sv.z, av.z, sv.w, av.w);
+    sa[3] = make_float4(sv.w, av.w, s4, a4);
+    return fminf(fminf(av.x, av.y), fminf(av.z, av.w));
 }
 
 template <int HY>
@@ -202,13 +202,13 @@ __device__ __forceinline__ float tile_stage_sa(const TileArgs &a, const PlaneCtx
                                                int y0, float *smt, int ndh)
 {
     const int hy = HY > 0 ? HY : a.hy;
-    const int ph = TL_H + 2 * hy, tsz = TL_PW * ph, q4 = TL_PW / 4;
+    const int ph = TL_H + 2 * hy, tsz = TL_PW * ph;
     float4 *SA = reinterpret_cast<float4 *>(smt + (size_t)ndh * tsz);
     const size_t npt = (size_t)a.np * a.nz;
     const float *Su = a.S + (size_t)l * npt + (size_t)c.ku * a.np;
     const float *Au = a.alpha + (size_t)l * npt + (size_t)c.ku * a.np;
     float amin = __int_as_float(0x7f800000);
-    for (int e = threadIdx.x; e < (ph - 1) * q4; e += TL_THREADS)
+    for (int e = threadIdx.x; e < ph * (TL_PW / 4); e += TL_THREADS)
         amin = fminf(amin, stage_sa_row(a, Su, Au, x0, y0, hy, e, SA));
     return amin;
 }
@@ -257,12 +257,15 @@ __device__ __forceinline__ void tile_item(const TileArgs &a, const PlaneCtx &c, 
         reinterpret_cast<int *>(sts)[tid] = __ldg(reinterpret_cast<const int *>(gst) + tid);
     const float hds_min = PP ? __ldg(&gst->hds_min) : a.hds_min;
     float amin = SA_DONE ? amin_in : __int_as_float(0x7f800000);
+    if (!SA_DONE)
+        for (int e = tid; e < ph * q4; e += TL_THREADS)
+            amin = fminf(amin, stage_sa_row(a, Su, Au, x0, y0, hy, e, SA));
     for (int e = tid; e < ph * q4; e += TL_THREADS) {
         const int r = e / q4, c4 = e % q4;
         const int gy = wrapi(y0 - hy + r, a.ny, a.wrap1);
         const int gx = wrapi(x0 - TL_HXP + 4 * c4, a.nx, a.wrap1);
         const size_t g = (size_t)gy * a.nx + gx;
-        if (!SA_DONE && r < ph - 1) amin = fminf(amin, stage_sa_row(a, Su, Au, x0, y0, hy, e, SA));
+
         const float *src0;
         size_t dstep;
         if (WAVE) {

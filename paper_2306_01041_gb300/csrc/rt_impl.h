@@ -210,6 +210,9 @@ std::vector<StencilD> regular_dir_stencils_d(const rt_grid *g, const double *u);
 // upwind tables of the given directions (Voronoi), built on the host and uploaded
 rt_status voronoi_build_tables(const rt_grid *g, int ndir, const double *dirs, VorTables &vt,
                                cudaStream_t st);
+// the upwind tables and levels of the grid's quadrature directions built on the device (the
+// default of rt_grid_create; RT_VORONOI_TABLES=host selects voronoi_build_tables)
+rt_status voronoi_build_tables_device(rt_grid *g, cudaStream_t st);
 // tables of one extra direction, cached on the grid
 rt_status voronoi_dir_tables_cached(rt_grid *g, const double *dir, VorTables **out,
                                     cudaStream_t st);

@@ -166,12 +166,26 @@ __global__ void __launch_bounds__(256) voronoi_levels_kernel(const Upwind *up, i
 
 using namespace rt;
 
-extern "C" rt_status rt_grid_build_tables_device(rt_grid_t g, void *stream)
+namespace rt {
+
+// The upwind tables and levels of the grid's quadrature directions, built on the device and
+// written into g->vt (host copies, slot order, device arrays; the arrays are reused when they
+// exist, so batches made from the grid keep valid pointers).
+rt_status voronoi_build_tables_device(rt_grid *g, cudaStream_t st)
 {
-    return guarded([&]() -> rt_status {
-        if (!g) return fail(RT_EINVAL, "null grid");
-        if (g->kind != RT_GRID_VORONOI) return fail(RT_EINVAL, "Voronoi grids only");
-        cudaStream_t st = (cudaStream_t)stream;
+    {
+        const int64_t n = g->nsites;
+        const int nd = g->ndir;
+        VorTables &vt0 = g->vt;
+        if (vt0.ndir != nd || vt0.h_up.size() != (size_t)nd * n) {
+            vt0.ndir = nd;
+            vt0.dirs.assign(g->dirs.begin(), g->dirs.end());
+            vt0.h_up.assign((size_t)nd * n, Upwind{});
+            vt0.h_level.assign((size_t)nd * n, 0);
+            vt0.h_upd.clear();
+        }
+    }
+    {
         const int64_t n = g->nsites;
         const int nd = g->ndir;
         const int64_t ne = g->nbr_off[n];
@@ -262,12 +276,24 @@ extern "C" rt_status rt_grid_build_tables_device(rt_grid_t g, void *stream)
         RT_TRY(voronoi_upload_slots(vt, n, st));
         g->max_levels = vt.max_levels;
         g->n_fallback = vt.n_fallback;
+        return RT_OK;
+    }
+}
+
+}  // namespace rt
+
+extern "C" rt_status rt_grid_build_tables_device(rt_grid_t g, void *stream)
+{
+    return guarded([&]() -> rt_status {
+        if (!g) return fail(RT_EINVAL, "null grid");
+        if (g->kind != RT_GRID_VORONOI) return fail(RT_EINVAL, "Voronoi grids only");
+        RT_TRY(voronoi_build_tables_device(g, (cudaStream_t)stream));
         // caches derived from the tables
         if (g->self_batch) rt_batch_destroy(g->self_batch);
         g->self_batch = nullptr;
         g->self_batch_nlam = 0;
         if (g->d_up_site)
-            RT_CUDA(cudaMemcpy(g->d_up_site, vt.h_up.data(), vt.h_up.size() * sizeof(Upwind),
+            RT_CUDA(cudaMemcpy(g->d_up_site, g->vt.h_up.data(), g->vt.h_up.size() * sizeof(Upwind),
                                cudaMemcpyHostToDevice));
         return RT_OK;
     });

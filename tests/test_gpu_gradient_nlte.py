@@ -157,3 +157,52 @@ def test_temperature_gradient_at_converged_populations(rt, case_fn):
         Tm[p] -= hp
         fd = (loss(Tp) - loss(Tm)) / (2 * hp)
         assert abs(gT[p] - fd) <= 1e-3 * max(scale[p], 1e-3 * np.abs(gT).max()), (p, gT[p], fd)
+
+
+def _atom_fields_3(A, f, pops, pick, chunk=1 << 17):
+    """alpha, S of the atom at the three wavelengths, evaluated in slices of points."""
+    n = f["T"].size
+    a3 = np.empty((3, n))
+    s3 = np.empty((3, n))
+    for q in range(0, n, chunk):
+        sl = slice(q, q + chunk)
+        a, s = A.alpha_S(f["T"][sl], f["rho"][sl], f["ne"][sl], pops[:, sl])
+        a3[:, sl], s3[:, sl] = a[pick], s[pick]
+    return f32(a3), f32(s3)
+
+
+@pytest.mark.parametrize("kind", ["regular_128", "voronoi_200k"])
+def test_adjoint_full_size_matches_oracle(rt, kind):
+    """The adjoint sweeps at the workload sizes: 128^3 points, and the 200 000-site grid sampled
+    from |dtau/dz|; the atom's line core and continua at LTE populations, a random weighting of
+    the mu = 1 map: dL/dalpha and dL/dS at every point against the oracle's adjoint."""
+    from oracle.physics import Atom
+    dirs, w = s4_quadrature()
+    atm = make_atmosphere(0)
+    if kind == "regular_128":
+        n = 128
+        f, (x, y, z, dx, dy) = regular_fields(n, n, n, atm)
+        G = rt.RegularGrid(n, n, n, dx, dy, z, dirs, w)
+    else:
+        from helpers import voronoi_grid
+        atm, vg, f = voronoi_grid(200000, "dtau", 9)
+        G = rt.VoronoiGrid(vg["xyz"], vg["nbr_off"], vg["nbr_idx"], vg["nbr_shift"], vg["box"],
+                           dirs, w)
+    f = {k: f32(v) for k, v in f.items()}
+    data = model_atom(np.min(f["ne"] / np.sqrt(f["T"])))
+    A = Atom(data, atm.kappa0)
+    pops = A.lte_pops(f["T"], f["ne"], f["nH"])
+    a3, s3 = _atom_fields_3(A, f, pops, _pick(data))
+    top = G.top_points()
+    gI = f32(np.random.default_rng(5).standard_normal((3, len(top))))
+    ga, gs = rt.formal_solution_adjoint(G, MU1, to_gpu(a3), to_gpu(s3), to_gpu(gI))
+    gI_full = np.zeros_like(a3)
+    gI_full[:, top] = gI
+    if kind == "regular_128":
+        ra, rs = oracle.sc_regular_adjoint(n, n, n, dx, dy, z, np.array(MU1), a3, s3, gI_full)
+    else:
+        tab = oracle.voronoi_tables(vg["xyz"], vg["nbr_off"], vg["nbr_idx"], vg["nbr_shift"],
+                                    vg["box"], np.array([MU1]), 7.0)
+        ra, rs = oracle.voronoi_adjoint(tab, 0, True, a3, s3, gI_full)
+    assert_parity(ga.cpu().numpy(), ra, rel=1e-4, floor=1e-6, what=f"{kind} dL/dalpha")
+    assert_parity(gs.cpu().numpy(), rs, rel=1e-4, floor=1e-6, what=f"{kind} dL/dS")

@@ -126,3 +126,27 @@ def test_lambda_iteration_converges(rt):
     assert conv and hist[-1] < 1e-3 and its < 300
     n = pops.cpu().double().numpy()
     np.testing.assert_allclose(n.sum(0), f["nH"], rtol=1e-5)
+
+
+def test_one_iteration_at_the_benchmark_size(rt):
+    """One Lambda iteration from LTE populations on the benchmark's 128^3 grid with the atom's 52
+    wavelengths and 24 directions (source terms, formal solution, rates, statistical
+    equilibrium): the GPU's populations against the oracle's at every point."""
+    from oracle.physics import Atom
+    n = 128
+    atm, f, (x, y, z, dx, dy), data = _setup(n, n, n)
+    A = Atom(data, atm.kappa0)
+    dirs, w = s4_quadrature()
+    f32 = {k: np.asarray(v, np.float32).astype(np.float64) for k, v in f.items()}
+    pops0 = A.lte_pops(f32["T"], f32["ne"], f32["nH"])
+    alpha, S = A.alpha_S(f32["T"], f32["rho"], f32["ne"], pops0)
+    J = OrcRegular(n, n, n, dx, dy, z, dirs, w).formal_solution(alpha, S)
+    del alpha, S
+    ref = A.statistical_equilibrium(A.rate_matrix(f32["T"], f32["ne"], J), f32["nH"])
+    del J
+    g = rt.RegularGrid(n, n, n, dx, dy, z, dirs, w)
+    ga, gm = rt.Atom(data, atm.kappa0), _gpu_atm(rt, f)
+    pops = rt.lte_populations(g, ga, gm)
+    its, hist, conv = rt.lambda_iterate(g, ga, gm, pops, max_iter=1, tol=0.0)
+    assert its == 1
+    assert_parity(pops.cpu().numpy(), ref, rel=1e-4, floor=0.0, what="128^3 iteration pops")

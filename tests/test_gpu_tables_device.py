@@ -30,9 +30,19 @@ def _unit_box(seed=1, n=400):
 
 
 def _check(rt, g, dirs=None, w=None):
+    """A grid created with the host table build (RT_VORONOI_TABLES=host), its tables rebuilt on
+    the device in place: both against the oracle; and a grid created with the default build."""
+    import os
     if dirs is None:
         dirs, w = s4_quadrature()
-    G = rt.VoronoiGrid(g["xyz"], g["nbr_off"], g["nbr_idx"], g["nbr_shift"], g["box"], dirs, w)
+    os.environ["RT_VORONOI_TABLES"] = "host"
+    try:
+        G = rt.VoronoiGrid(g["xyz"], g["nbr_off"], g["nbr_idx"], g["nbr_shift"], g["box"], dirs,
+                           w)
+    finally:
+        del os.environ["RT_VORONOI_TABLES"]
+    default = rt.VoronoiGrid(g["xyz"], g["nbr_off"], g["nbr_idx"], g["nbr_shift"], g["box"], dirs,
+                             w).tables()
     host = G.tables()
     ml, nfb = G.max_levels, G.n_fallback
     G.build_tables_device()
@@ -45,6 +55,8 @@ def _check(rt, g, dirs=None, w=None):
     np.testing.assert_allclose(dev["len"], ref["len"], rtol=1e-6)
     np.testing.assert_array_equal(dev["k"], host["k"])
     np.testing.assert_array_equal(dev["level"], host["level"])
+    for key in ("k", "w", "len", "level"):
+        np.testing.assert_array_equal(default[key], dev[key])
     assert G.n_fallback == ref["n_fallback"] == nfb
     assert G.max_levels == ref["level"].max() + 1 == ml
     return G, dirs, w, ref

@@ -114,8 +114,8 @@ def test_persistent_sweep_equals_level_launches(rt, monkeypatch, bc, nlam, n):
         n0 = rt.kernel_launches()
         out[mode] = rt.formal_solution(G, to_gpu(a), to_gpu(s), bc=bc).cpu()
         launched = rt.kernel_launches() - n0
-        if mode == "persistent":   # (S, alpha) pair transpose, sweep, J reduction, transpose
-            assert launched == 4, launched
+        if mode == "persistent":   # (S, alpha) packing, sweep, J reduction into [nlam][n]
+            assert launched == 3, launched
         torch.cuda.synchronize()
     assert torch.equal(out["persistent"], out["levels"])
     tab = oracle.voronoi_tables(g["xyz"], g["nbr_off"], g["nbr_idx"], g["nbr_shift"], g["box"],
