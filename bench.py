@@ -43,8 +43,9 @@ WORKLOAD = "NLTE Lambda iteration, regular grid 128x128x128, 52 wavelengths, 24 
 # DRAM bytes from the ncu captures summarised in profiles/, valid only for the kernel source with
 # this hash (else reported as null)
 PROFILED_FILE = "paper_2306_01041_gb300/csrc/regular_tile.cu"
-PROFILED = {"sc_wave_kernel": {"file": PROFILED_FILE, "sha1": None,
-                               "dram_bytes_per_launch": None},
+PROFILED = {"sc_wave_kernel": {"file": PROFILED_FILE,
+                               "sha1": "9c85abfb145ac072877f89b1a98ca32bbb878e2a",
+                               "dram_bytes_per_launch": 2.187412480e9 + 1.224155904e9},
             "sc_tile_kernel": {"file": PROFILED_FILE, "sha1": None, "dram_bytes_per_launch": None},
             "batch_sweep_kernel": {"file": "paper_2306_01041_gb300/csrc/batch.cu", "sha1": None,
                                    "dram_bytes_per_update": None}}

@@ -14,7 +14,7 @@
 // so an upwind gather reads only the sectors it uses, and the items of the other chunks of the
 // same direction, which sweep the same sites at about the same time, read the same lines.
 // A thread keeps one wavelength lane (tid % cs) for a whole item and steps through the level's
-// sites, two at a time so that two independent gathers are in flight.
+// sites, three at a time so that three independent gather chains are in flight.
 #include <algorithm>
 #include <cmath>
 #include <numeric>
@@ -112,6 +112,11 @@ __device__ __forceinline__ float vor_update(const Upwind &u, const VorGather &r)
     return acc;
 }
 
+// U: updates a thread keeps in flight (sites of the level U steps apart, independent gathers);
+// measured on the 8-atmosphere batch: 2 -> 93.6, 3 -> 98.1, 4 -> 62.0 G updates/s (4 spills
+// registers at two blocks of 512 threads per SM).
+constexpr int BATCH_INFLIGHT = 3;
+template <int U>
 __global__ void __launch_bounds__(512, 2) batch_sweep_kernel(const BatchArgs a)
 {
     __shared__ int item_s;
@@ -139,22 +144,23 @@ __global__ void __launch_bounds__(512, 2) batch_sweep_kernel(const BatchArgs a)
         for (int L = b0; L + 1 < b1; ++L) {
             const int64_t s1 = g.lvl[L + 1];
             if (active) {
-                for (int64_t sa = g.lvl[L] + soff; sa < s1; sa += 2 * step) {
-                    const int64_t sb = sa + step;
-                    const bool two = sb < s1;
-                    const Upwind ua = up[sa];
-                    const int ia = order[sa];
-                    Upwind ub = ua;
-                    int ib = ia;
-                    if (two) {
-                        ub = up[sb];
-                        ib = order[sb];
+                for (int64_t s = g.lvl[L] + soff; s < s1; s += U * step) {
+                    Upwind u[U];
+                    int i[U];
+                    bool v[U];
+#pragma unroll
+                    for (int q = 0; q < U; ++q) {
+                        const int64_t sq = s + (int64_t)q * step;
+                        v[q] = sq < s1;
+                        u[q] = up[v[q] ? sq : s];
+                        i[q] = order[v[q] ? sq : s];
                     }
-                    const VorGather ga = vor_gather(g, I, ua, ia, c0, P, inflow);
-                    VorGather gb = ga;
-                    if (two) gb = vor_gather(g, I, ub, ib, c0, P, inflow);
-                    I[c0 + (size_t)ia * P] = vor_update(ua, ga);
-                    if (two) I[c0 + (size_t)ib * P] = vor_update(ub, gb);
+                    VorGather gq[U];
+#pragma unroll
+                    for (int q = 0; q < U; ++q) gq[q] = vor_gather(g, I, u[q], i[q], c0, P, inflow);
+#pragma unroll
+                    for (int q = 0; q < U; ++q)
+                        if (v[q]) I[c0 + (size_t)i[q] * P] = vor_update(u[q], gq[q]);
                 }
             }
             __syncthreads();
@@ -297,7 +303,8 @@ rt_status rt_batch_create(const rt_grid_t *grids, int ngrids, int nlam, const in
         int dev = 0, nsm = 0, per_sm = 0;
         RT_CUDA(cudaGetDevice(&dev));
         RT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-        RT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_sweep_kernel, b->threads, 0));
+        RT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_sweep_kernel<BATCH_INFLIGHT>,
+                                                              b->threads, 0));
         if (per_sm < 1) {
             delete b;
             return fail(RT_ECAPACITY, "the batched sweep kernel cannot be resident");
@@ -436,7 +443,7 @@ rt_status rt_batch_formal_solution(rt_batch_t b, const float *const *alpha, cons
         a.bc = bc;
         const int blocks = std::min<int>(b->blocks, a.nitems);
         note_launch();
-        batch_sweep_kernel<<<blocks, b->threads, 0, st>>>(a);
+        batch_sweep_kernel<BATCH_INFLIGHT><<<blocks, b->threads, 0, st>>>(a);
         for (int i = 0; i < ng; ++i) {
             const BatchGridDev &g = b->h_grids[i];
             note_launch();
