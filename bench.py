@@ -43,7 +43,9 @@ WORKLOAD = "NLTE Lambda iteration, regular grid 128x128x128, 52 wavelengths, 24 
 # DRAM bytes from the ncu captures summarised in profiles/, valid only for the kernel source with
 # this hash (else reported as null)
 PROFILED_FILE = "paper_2306_01041_gb300/csrc/regular_tile.cu"
-PROFILED = {"sc_wave_kernel": {"file": PROFILED_FILE,
+PROFILED = {"sc_pipe_kernel": {"file": "paper_2306_01041_gb300/csrc/regular_pipe.cu",
+                               "sha1": None, "dram_bytes_per_launch": None},
+            "sc_wave_kernel": {"file": PROFILED_FILE,
                                "sha1": "9c85abfb145ac072877f89b1a98ca32bbb878e2a",
                                "dram_bytes_per_launch": 2.187412480e9 + 1.224155904e9},
             "sc_tile_kernel": {"file": PROFILED_FILE, "sha1": None, "dram_bytes_per_launch": None},
@@ -264,15 +266,18 @@ def run_gpu(args):
     updates = npt * NDIR * nlam
     value = updates * world / (ms * 1e-3) / 1e9
     fs_ms = statistics.mean(fs_times)
-    # the formal-solution graph is one persistent wavefront launch (sc_wave_kernel) or, when that
-    # path does not apply, one launch per plane step and hemisphere (sc_tile_kernel) plus the two
-    # boundary planes; the achieved rate is the interior updates over the graph's event time
+    # the formal-solution graph is one persistent wavefront launch (sc_pipe_kernel on periodic
+    # grids whose tiles its staging covers, else sc_wave_kernel) or, when neither applies, one
+    # launch per plane step and hemisphere (sc_tile_kernel) plus the two boundary planes; the
+    # achieved rate is the interior updates over the graph's event time
     interior_ops = OPS_PER_UPDATE * NX * NY * (NZ - 1) * NDIR * nlam
     if args.scheme == "face":
         # face_sweep_kernel, then the fixed-order sum of the two hemispheres' J partials
         kname, per_launch_ms = "face_sweep_kernel", fs_ms
     elif launches[1] == 1:
-        kname, per_launch_ms = "sc_wave_kernel", fs_ms
+        kname = ("sc_wave_kernel" if os.environ.get("RT_REGULAR_SWEEP", "pipe") != "pipe"
+                 else "sc_pipe_kernel")
+        per_launch_ms = fs_ms
     else:
         kname, per_launch_ms = "sc_tile_kernel", fs_ms / (2 * (NZ - 1))
     achieved = interior_ops / (fs_ms * 1e-3) / 1e12

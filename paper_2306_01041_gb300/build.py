@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "librt.so")
-SOURCES = ["api.cu", "regular.cu", "regular_tile.cu", "voronoi.cu",
+SOURCES = ["api.cu", "regular.cu", "regular_tile.cu", "regular_pipe.cu", "voronoi.cu",
            "nlte.cu", "batch.cu", "noalloc.cu", "ali.cu", "idw.cu", "ng.cu",
            "regular_face.cu", "sampling.cu", "tables.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -79,6 +79,8 @@ static Stencil plane_stencil(double dz, const double *u, double dx, double dy, i
     s.w3 = (float)(tx * ty);
     s.hds = (float)(0.5 * ds);
     s.pad = 0.f;
+    s.tx = (float)tx;
+    s.ty = (float)ty;
     return s;
 }
 

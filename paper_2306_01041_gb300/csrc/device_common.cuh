@@ -47,6 +47,16 @@ __device__ __forceinline__ void lin_weights(float d, float &ex, float &w0, float
     }
 }
 
+// Interval weights for d >= 0.1 only: the same arithmetic as the d >= 0.1 branch of lin_weights.
+__device__ __forceinline__ void lin_weights_thick(float d, float &ex, float &w0, float &w1)
+{
+    ex = exp_neg(d);
+    const float e0 = 1.0f - ex;
+    const float q = __fmul_rn(e0, rcp_fast(d));
+    w1 = 1.0f - q;
+    w0 = q - ex;
+}
+
 // ---- two points at once: packed FP32 pairs (the f32x2 arithmetic of sm_100 and later) ---------
 // The same operations as the scalar forms above, on the two components of a float2 (one rounding
 // per component, as the scalar FMA): the stencil weights of a direction are shared by a thread's

@@ -83,16 +83,6 @@ struct WaveSt {
 };
 static_assert(sizeof(WaveSt) == 32, "WaveSt is two float4");
 
-// Interval weights for d >= 0.1 only: the same arithmetic as the d >= 0.1 branch of lin_weights.
-__device__ __forceinline__ void lin_weights_thick(float d, float &ex, float &w0, float &w1)
-{
-    ex = exp_neg(d);
-    const float e0 = 1.0f - ex;
-    const float q = __fmul_rn(e0, rcp_fast(d));
-    w1 = 1.0f - q;
-    w0 = q - ex;
-}
-
 // Per-point updates of one staged item for every direction.  THICK: every interval of the item
 // has d >= 0.1, so only the exact interval weights are evaluated.  The thread's two points (tile
 // rows R and R + 1) share every per-direction coefficient, so their arithmetic runs as packed
@@ -601,12 +591,20 @@ static bool uniform_stencils(const rt_grid *g)
     return true;
 }
 
+size_t regular_wave_table_offset(const rt_grid *g)
+{
+    return (size_t)g->nz * 2 * 12 * sizeof(WaveSt);
+}
+
 size_t regular_wave_scratch(const rt_grid *g, int nlam)
 {
+    // the tile-major ring slots and flags of sc_wave_kernel, or the pipelined sweep's rings,
+    // whichever is larger
     const size_t ntiles = (size_t)((g->nx + TL_W - 1) / TL_W) * ((g->ny + TL_H - 1) / TL_H);
-    const size_t plane = (size_t)nlam * ntiles * 12 * TL_W * TL_H;   // tile-major ring slot
+    const size_t plane = (size_t)nlam * ntiles * 12 * TL_W * TL_H;
     const size_t nflags = 2 * (size_t)g->nz * nlam * ntiles;
-    return 4 * plane * sizeof(float) + (nflags + 64) * sizeof(int);
+    return std::max(4 * plane * sizeof(float) + (nflags + 64) * sizeof(int),
+                    regular_pipe_scratch(g, nlam));
 }
 
 rt_status regular_wave_prepare(rt_grid *g, cudaStream_t st)
@@ -615,6 +613,7 @@ rt_status regular_wave_prepare(rt_grid *g, cudaStream_t st)
     if (!tile_geometry(g, hy) || g->dir_up.size() != 12 || g->dir_dn.size() != 12 || g->nz < 3)
         return RT_OK;
     std::vector<WaveSt> t((size_t)g->nz * 2 * 12, WaveSt{0, 0, 0, 0, 0, 0, 0, 0});
+    std::vector<PlaneStencil> rt_((size_t)g->nz * 2 * 12, PlaneStencil{});
     const std::vector<int> *hs[2] = {&g->dir_up, &g->dir_dn};
     for (int k = 0; k < g->nz; ++k)
         for (int h = 0; h < 2; ++h) {
@@ -632,11 +631,25 @@ rt_status regular_wave_prepare(rt_grid *g, cudaStream_t st)
                 e[d].wd = (float)g->wdir[q];
                 e[d].off = sc.ay * TL_PW + sc.ax;
                 hmin = d == 0 ? sc.hds : std::min(hmin, sc.hds);
+                PlaneStencil &r = rt_[((size_t)k * 2 + h) * 12 + d];
+                r.tx = make_float2(sc.tx, sc.tx);
+                r.ux = make_float2(1.0f - sc.tx, 1.0f - sc.tx);
+                r.ty = make_float2(sc.ty, sc.ty);
+                r.uy = make_float2(1.0f - sc.ty, 1.0f - sc.ty);
+                r.hds = sc.hds;
+                r.wd = (float)g->wdir[q];
+                r.off = sc.ay * TL_PW + sc.ax;
             }
-            for (int d = 0; d < 12; ++d) e[d].hds_min = hmin;
+            for (int d = 0; d < 12; ++d) {
+                e[d].hds_min = hmin;
+                rt_[((size_t)k * 2 + h) * 12 + d].hds_min = hmin;
+            }
         }
-    g->h_wave_st.resize(t.size() * sizeof(WaveSt));
-    std::memcpy(g->h_wave_st.data(), t.data(), g->h_wave_st.size());
+    // [WaveSt table][PlaneStencil table]
+    g->h_wave_st.resize(t.size() * sizeof(WaveSt) + rt_.size() * sizeof(PlaneStencil));
+    std::memcpy(g->h_wave_st.data(), t.data(), t.size() * sizeof(WaveSt));
+    std::memcpy(g->h_wave_st.data() + t.size() * sizeof(WaveSt), rt_.data(),
+                rt_.size() * sizeof(PlaneStencil));
     RT_CUDA(cudaMalloc(&g->d_wave_st, g->h_wave_st.size()));
     RT_CUDA(cudaMemcpyAsync(g->d_wave_st, g->h_wave_st.data(), g->h_wave_st.size(),
                             cudaMemcpyHostToDevice, st));
@@ -737,6 +750,8 @@ rt_status regular_tile_sweep(rt_grid *g, int nlam, const float *alpha, const flo
                              float *J, float *buf0, float *buf1, cudaStream_t st, bool *done)
 {
     *done = false;
+    RT_TRY(regular_pipe_sweep(g, nlam, alpha, S, bc, J, st, done));
+    if (*done) return RT_OK;
     int hy;
     if (bc == RT_BC_ARRAY || !tile_plan(g, hy)) return RT_OK;
     if (!aligned16(alpha) || !aligned16(S)) return RT_OK;

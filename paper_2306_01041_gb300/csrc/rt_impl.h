@@ -63,7 +63,20 @@ struct Stencil {
     float w0, w1, w2, w3;
     float hds;
     float pad;
+    float tx, ty;     // fractional offsets: w0 = (1 - tx)(1 - ty), w1 = tx (1 - ty), w2 = (1 - tx) ty
 };
+
+// One direction's stencil on one plane as the pipelined regular sweep reads it (three 16-byte
+// loads): (v, v) pairs of the fractional offsets and of their complements, half path length,
+// quadrature weight, corner displacement in the staged tile (ay * 40 + ax) and the plane's smallest
+// half path length over the hemisphere.
+struct PlaneStencil {
+    float2 tx, ux, ty, uy;
+    float hds, wd;
+    int off;
+    float hds_min;
+};
+static_assert(sizeof(PlaneStencil) == 48, "PlaneStencil is three float4");
 
 // FP64 stencil of one direction, for the adjoint's forward recomputation.
 struct StencilD {
@@ -177,6 +190,13 @@ rt_status voronoi_upload_slots(VorTables &vt, int64_t n, cudaStream_t st);
 rt_status regular_tile_sweep(rt_grid *g, int nlam, const float *alpha, const float *S, int bc,
                              float *J, float *buf0, float *buf1, cudaStream_t st, bool *done);
 size_t regular_wave_scratch(const rt_grid *g, int nlam);
+// byte offset, in the wavefront sweep's device table, of the per-plane stencil table with
+// fractional offsets (48-byte entries [nz][2][12])
+size_t regular_wave_table_offset(const rt_grid *g);
+// pipelined wavefront sweep (producer warp, tensor copies); *done = false when it does not apply
+rt_status regular_pipe_sweep(rt_grid *g, int nlam, const float *alpha, const float *S, int bc,
+                             float *J, cudaStream_t st, bool *done);
+size_t regular_pipe_scratch(const rt_grid *g, int nlam);
 // Voronoi: builds what the formal solution of nlam wavelengths allocates on first use (call
 // outside stream capture)
 rt_status voronoi_prepare(rt_grid *g, int nlam);
