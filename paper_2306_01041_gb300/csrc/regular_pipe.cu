@@ -64,7 +64,7 @@ struct PipeArgs {
     float *J;
     unsigned *err;
     int *queue;
-    int *done;             // [2][nz][nlam][ntiles]: consumer warps that finished the item
+    int *done;             // [2][nz][nlam][ntiles]: 1 once the item is published
     float wd[2][NDH];      // quadrature weights per hemisphere (boundary planes)
     int nx, ny, nz, np, nlam, hy, px, py, tiles_x, ntiles, lchunk, bc;
 };
@@ -611,11 +611,13 @@ rt_status regular_pipe_sweep(rt_grid *g, int nlam, const float *alpha, const flo
     RT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     const int blocks = per_sm * nsm;
     {
-        // wavelengths per chunk: a plane step of a chunk holds more items than the blocks hold in
-        // flight (two each), so that the upwind items of a claimed item are normally done, and no
-        // more, so that the chunk's rings stay in L2; chunks of equal size.  RT_WAVE_LCHUNK
-        // overrides.
-        const int target = std::max(1, (5 * blocks + 2 * a.ntiles - 1) / (2 * a.ntiles));
+        // wavelengths per chunk: a plane step of a chunk holds several times the items that the
+        // blocks hold in flight (three each: two staged, one claimed), so that the upwind items
+        // of a claimed item are normally done; chunks of equal size.  At 128 x 128 and 52
+        // wavelengths this is one chunk: measured 5.35 ms against 5.67 ms with two chunks of 26
+        // and 6.57 ms with three, although the rings of all wavelengths then exceed the L2 share
+        // (L2 eviction hints that favour the ring made it slower).  RT_WAVE_LCHUNK overrides.
+        const int target = std::max(1, (4 * blocks + a.ntiles - 1) / a.ntiles);
         const int nch = std::max(1, (nlam + target / 2) / target);
         int lc = (nlam + nch - 1) / nch;
         if (const char *e = std::getenv("RT_WAVE_LCHUNK")) lc = std::atoi(e);
