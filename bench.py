@@ -48,8 +48,15 @@ PROFILED = {"sc_pipe_kernel": {"file": "paper_2306_01041_gb300/csrc/regular_pipe
                                "dram_bytes_per_launch": 4.937694208e9 + 14.107289856e9},
             "sc_wave_kernel": {"file": PROFILED_FILE, "sha1": None, "dram_bytes_per_launch": None},
             "sc_tile_kernel": {"file": PROFILED_FILE, "sha1": None, "dram_bytes_per_launch": None},
-            "batch_sweep_kernel": {"file": "paper_2306_01041_gb300/csrc/batch.cu", "sha1": None,
-                                   "dram_bytes_per_update": None}}
+            "batch_sweep_kernel": {"file": "paper_2306_01041_gb300/csrc/batch.cu",
+                                   "sha1": "15c9bee6f032c97d7e7092c3ed8c86d5a5fc8775",
+                                   # measured on the first two atmospheres (146 M updates; the
+                                   # 8-atmosphere launch is larger than a capture should hold),
+                                   # per update, scaled to the launch by its updates
+                                   "dram_bytes_per_update": (1.350062e9 + 0.619866e9) / 146.016e6},
+            "face_sweep_kernel": {"file": "paper_2306_01041_gb300/csrc/regular_face.cu",
+                                  "sha1": "82c92181450fa95b2f1cef004e9929a650fa9c8b",
+                                  "dram_bytes_per_launch": 21.575351296e9 + 11.012112128e9}}
 
 # Algorithmic FP32 work of one point-direction-wavelength update of the regular sweep, counted in
 # lane operations (an FMA counts once): three bilinear interpolations (6 each), dtau (2), interval
