@@ -129,14 +129,20 @@ def test_full_size_128cubed_sampled_wavelengths(rt):
                                               ((64, 64, 40), 4, "stretched"),
                                               ((36, 40, 19), 3, "stretched"),
                                               ((128, 64, 33), 3, "stretched"),
-                                              ((64, 96, 20), 2, "uniform")])
+                                              ((64, 96, 20), 2, "uniform"),
+                                              ((32, 32, 10), 2, "uniform"),
+                                              ((64, 65, 12), 2, "uniform"),
+                                              ((64, 67, 12), 2, "uniform")])
 def test_sweep_variants_match_each_other_and_oracle(rt, monkeypatch, shape, nlam, zkind):
     """The regular-grid sweeps -- the persistent wavefront kernel (default wherever the staged
     tile covers every stencil; constant-bank stencils on uniform z, per-plane stencil tables on
     stretched z; a thread's two points as packed FP32 pairs), shared-memory tiles per plane, and
     the plain per-plane kernel -- compute the same updates: each matches the oracle and the
     others (up to FMA contraction).  "rough" z steps reach beyond the tile halo, where the default falls
-    back to the plain kernel."""
+    back to the plain kernel.  The uniform steps reach 3 rows: 32 x 32 is a single tile column
+    whose ring halo copies wrap onto the tile itself; with 65 rows the last of five tile rows is
+    shorter than the reach, so the warp-specialised sweep gives way to the other persistent one,
+    and with 67 rows it is not."""
     import torch
     nx, ny, nz = shape
     rng = np.random.default_rng(21)
