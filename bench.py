@@ -55,7 +55,7 @@ PROFILED = {"sc_pipe_kernel": {"file": "paper_2306_01041_gb300/csrc/regular_pipe
                                    # per update, scaled to the launch by its updates
                                    "dram_bytes_per_update": (1.350062e9 + 0.619866e9) / 146.016e6},
             "face_sweep_kernel": {"file": "paper_2306_01041_gb300/csrc/regular_face.cu",
-                                  "sha1": "82c92181450fa95b2f1cef004e9929a650fa9c8b",
+                                  "sha1": None,
                                   "dram_bytes_per_launch": 21.575351296e9 + 11.012112128e9}}
 
 # Algorithmic FP32 work of one point-direction-wavelength update of the regular sweep, counted in

@@ -91,10 +91,28 @@ __global__ void __launch_bounds__(FACE_MAXW * 32, 1) face_sweep_kernel(FaceArgs 
 {
     extern __shared__ float sm[];
     __shared__ FaceDir sdir[FACE_MAXW];
+    // J of a plane: per direction of the group its plane buffer, weight and slot among the
+    // directions whose planes are held transposed (-1: held as [y][x])
+    __shared__ const float *sbq[FACE_MAXW];
+    __shared__ float swq[FACE_MAXW];
+    __shared__ int sxq[FACE_MAXW], sxinv[FACE_MAXW];
     const int lam = blockIdx.x, grp = blockIdx.y;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     const int d0 = a.first[grp], nd = a.first[grp + 1] - d0;
     if (threadIdx.x < nd) sdir[threadIdx.x] = a.dirs[d0 + threadIdx.x];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int xi = 0;
+        for (int q = 0; q < nd; ++q) {
+            sbq[q] = a.buf + ((size_t)lam * a.ndir + sdir[q].dir) * (size_t)a.nx * a.ny;
+            swq[q] = sdir[q].w;
+            sxq[q] = -1;
+            if (sdir[q].a_is_x) {
+                sxinv[xi] = q;
+                sxq[q] = xi++;
+            }
+        }
+    }
     __syncthreads();
     const int nx = a.nx, ny = a.ny, nz = a.nz, np = nx * ny;
     const size_t npt = (size_t)np * nz;
@@ -122,39 +140,39 @@ __global__ void __launch_bounds__(FACE_MAXW * 32, 1) face_sweep_kernel(FaceArgs 
     };
 
     // J partial of plane k: sum over the group's directions in group order
+    // transposed directions of the group, and the 32 x 32 tiles the shared tile buffer (room for
+    // wpb transposed tiles) holds at once: the tiles of one batch share each pair of barriers
+    int nxd = 0;
+    for (int q = 0; q < nd; ++q) nxd += sxq[q] >= 0;
+    const int tpb = nxd ? max(1, wpb / nxd) : 4;
+    const int tcx = (nx + 31) >> 5, ntile = tcx * ((ny + 31) >> 5);
     auto j_plane = [&](int k) {
         float *Jk = Jout + (size_t)k * np;
-        for (int tj = 0; tj < ny; tj += 32)
-            for (int ti = 0; ti < nx; ti += 32) {
-                int xi = 0;
-                for (int q = 0; q < nd; ++q) {
-                    if (!sdir[q].a_is_x) continue;
-                    const float *bq = a.buf + ((size_t)lam * a.ndir + sdir[q].dir) * np;
-                    for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
-                        const int r = e >> 5, c = e & 31, i = ti + r, j = tj + c;
-                        tile[(xi * 32 + r) * 33 + c] = (i < nx && j < ny) ? bq[(size_t)i * ny + j] : 0.f;
-                    }
-                    ++xi;
-                }
-                __syncthreads();
-                for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
-                    const int r = e >> 5, c = e & 31, i = ti + c, j = tj + r;
-                    if (i >= nx || j >= ny) continue;
-                    float acc = 0.f;
-                    int x2 = 0;
-                    for (int q = 0; q < nd; ++q) {
-                        float v;
-                        if (sdir[q].a_is_x)
-                            v = tile[(x2++ * 32 + c) * 33 + r];
-                        else
-                            v = a.buf[((size_t)lam * a.ndir + sdir[q].dir) * np + (size_t)j * nx + i];
-                        acc = fmaf(sdir[q].w, v, acc);
-                    }
-                    if (!isfinite(acc)) flag_error(a.err, ERR_NAN);
-                    Jk[(size_t)j * nx + i] = acc;
-                }
-                __syncthreads();
+        for (int t0 = 0; t0 < ntile; t0 += tpb) {
+            const int nt = min(tpb, ntile - t0);
+            for (int e = threadIdx.x; e < nt * nxd * 1024; e += blockDim.x) {
+                const int tb = e / (nxd * 1024), xi = (e / 1024) % nxd, r = (e >> 5) & 31, c = e & 31;
+                const int t = t0 + tb, i = (t % tcx) * 32 + r, j = (t / tcx) * 32 + c;
+                tile[((tb * nxd + xi) * 32 + r) * 33 + c] =
+                    (i < nx && j < ny) ? sbq[sxinv[xi]][i * ny + j] : 0.f;
             }
+            __syncthreads();
+            for (int e = threadIdx.x; e < nt * 1024; e += blockDim.x) {
+                const int tb = e >> 10, r = (e >> 5) & 31, c = e & 31, t = t0 + tb;
+                const int i = (t % tcx) * 32 + c, j = (t / tcx) * 32 + r;
+                if (i >= nx || j >= ny) continue;
+                const int f = j * nx + i;
+                float acc = 0.f;
+                for (int q = 0; q < nd; ++q) {   // the group's order
+                    const int xi = sxq[q];
+                    const float v = xi >= 0 ? tile[((tb * nxd + xi) * 32 + c) * 33 + r] : sbq[q][f];
+                    acc = fmaf(swq[q], v, acc);
+                }
+                if (!isfinite(acc)) flag_error(a.err, ERR_NAN);
+                Jk[f] = acc;
+            }
+            __syncthreads();
+        }
     };
 
     // the wall plane the rays enter through
