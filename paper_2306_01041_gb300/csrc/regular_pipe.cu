@@ -109,9 +109,8 @@ __device__ __forceinline__ void mbar_arrive_tx(uint64_t *b, unsigned bytes)
                  :: "r"(smem_u32(b)), "r"(bytes) : "memory");
 }
 
-// Test for the completion of the phase of the given parity; the warp may be suspended up to about
-// 10 microseconds while the phase is still open (it resumes when the phase completes), so that a
-// waiting warp takes no issue slots from the others.
+// Test for the completion of the phase of the given parity, with a suspend-time hint of 10
+// microseconds (the hardware may hold the thread while the phase is open, up to the hint).
 __device__ __forceinline__ bool mbar_test(uint64_t *b, unsigned parity)
 {
     uint32_t ok;
