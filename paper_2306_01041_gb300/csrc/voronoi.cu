@@ -145,6 +145,25 @@ static bool self_batch_applies(int bc, const float *I_dir)
     return bc != RT_BC_ARRAY && !I_dir;
 }
 
+// The batch keeps (S, alpha) and one intensity array per direction for all its wavelengths,
+// (2 + ndir) n P floats with P the wavelengths rounded up to 8.  When that exceeds half the free
+// device memory (RT_VORONOI_BATCH_MB sets another budget), the batch is built for the largest
+// divisor of nlam that fits and the formal solution runs the wavelengths in that many equal
+// chunks: every wavelength is computed the same way, so J is the same.
+static int self_batch_chunk(const rt_grid *g, int nlam)
+{
+    size_t budget = 0, total = 0;
+    if (cudaMemGetInfo(&budget, &total) != cudaSuccess) return nlam;
+    budget /= 2;
+    if (const char *e = std::getenv("RT_VORONOI_BATCH_MB")) budget = (size_t)std::atoll(e) << 20;
+    for (int d = nlam; d > 1; --d) {
+        if (nlam % d) continue;
+        const size_t bytes = (size_t)(2 + g->ndir) * g->nsites * (size_t)((d + 7) & ~7) * 4;
+        if (bytes <= budget) return d;
+    }
+    return 1;
+}
+
 rt_status voronoi_prepare(rt_grid *g, int nlam)
 {
     if (!self_batch_applies(RT_BC_THERMAL, nullptr)) return RT_OK;
@@ -152,7 +171,7 @@ rt_status voronoi_prepare(rt_grid *g, int nlam)
     if (g->self_batch) rt_batch_destroy(g->self_batch);
     g->self_batch = nullptr;
     rt_grid_t gg = g;
-    RT_TRY(rt_batch_create(&gg, 1, nlam, nullptr, 0, &g->self_batch));
+    RT_TRY(rt_batch_create(&gg, 1, self_batch_chunk(g, nlam), nullptr, 0, &g->self_batch));
     g->self_batch_nlam = nlam;
     return RT_OK;
 }
@@ -167,9 +186,14 @@ rt_status voronoi_formal_solution(rt_grid *g, int nlam, const float *alpha, cons
         // building the batch allocates: not while a stream is being captured
         if (cap == cudaStreamCaptureStatusNone) RT_TRY(voronoi_prepare(g, nlam));
         if (g->self_batch && g->self_batch_nlam == nlam) {
-            const float *al[1] = {alpha}, *Sl[1] = {S};
-            float *Jl[1] = {J};
-            return rt_batch_formal_solution(g->self_batch, al, Sl, bc, Jl, st);
+            const int nlc = batch_nlam(g->self_batch);   // a divisor of nlam
+            const size_t n = (size_t)g->nsites;
+            for (int l0 = 0; l0 < nlam; l0 += nlc) {
+                const float *al[1] = {alpha + l0 * n}, *Sl[1] = {S + l0 * n};
+                float *Jl[1] = {J + l0 * n};
+                RT_TRY(rt_batch_formal_solution(g->self_batch, al, Sl, bc, Jl, st));
+            }
+            return RT_OK;
         }
     }
     const int64_t n = g->nsites;

@@ -122,3 +122,30 @@ def test_persistent_sweep_equals_level_launches(rt, monkeypatch, bc, nlam, n):
                                 dirs, 7.0)
     Jr = oracle.voronoi_fs(tab, dirs, w, a, s, bc=bc)
     assert_parity(out["persistent"].numpy(), Jr, what="J persistent")
+
+
+def test_wavelength_chunks_give_the_same_J(rt, monkeypatch):
+    """When the per-direction intensities of all wavelengths exceed the device-memory budget, the
+    single-grid sweep runs the wavelengths in equal chunks (a divisor of their count): J is bit
+    for bit the one pass's, and matches the oracle."""
+    import torch
+    g = _small(4, 3000)
+    dirs, w = s4_quadrature()
+    n, nlam = len(g["xyz"]), 12
+    rng = np.random.default_rng(8)
+    a = 10.0 ** rng.uniform(-3, 2, (nlam, n))
+    s = rng.uniform(0.5, 2.0, (nlam, n))
+    ag, sg = to_gpu(a), to_gpu(s)
+    monkeypatch.delenv("RT_VORONOI_BATCH_MB", raising=False)
+    J1 = rt.formal_solution(_grid(rt, g, dirs, w), ag, sg)
+    # 26 floats per site and padded wavelength (a multiple of 8): 3000 sites x 8 is 2.5 MB, so a
+    # 3 MB budget allows chunks of 6 (two chunks); below 2.5 MB single wavelengths remain
+    for mb in ("3", "1"):
+        monkeypatch.setenv("RT_VORONOI_BATCH_MB", mb)
+        Jc = rt.formal_solution(_grid(rt, g, dirs, w), ag, sg)
+        torch.cuda.synchronize()
+        assert torch.equal(Jc, J1), mb
+    tab = oracle.voronoi_tables(g["xyz"], g["nbr_off"], g["nbr_idx"], g["nbr_shift"], g["box"],
+                                dirs, 7.0)
+    Jr = oracle.voronoi_fs(tab, dirs, w, a, s)
+    assert_parity(J1.cpu().numpy(), Jr, what="J")
