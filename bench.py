@@ -281,7 +281,7 @@ def run_gpu(args):
     # achieved rate is the interior updates over the graph's event time
     interior_ops = OPS_PER_UPDATE * NX * NY * (NZ - 1) * NDIR * nlam
     if args.scheme == "face":
-        # face_sweep_kernel, then the fixed-order sum of the two hemispheres' J partials
+        # face_sweep_kernel, then the J pass over the planes it kept (face_j_kernel)
         kname, per_launch_ms = "face_sweep_kernel", fs_ms
     elif launches[1] == 1:
         kname = ("sc_wave_kernel" if os.environ.get("RT_REGULAR_SWEEP", "pipe") != "pipe"

@@ -16,9 +16,9 @@
 // k -/+ 1 (and, on the plane face, line a of plane k -/+ 1), staged in a two-line ring in shared
 // memory, while the next line's loads are in flight.  Directions whose lines run along x read S and
 // alpha from copies transposed to [nlam][nz][x][y] once per call, so that every line load is
-// contiguous.  The plane buffer is updated in place: line a
-// of the previous plane is no longer needed once line a of this plane is computed (the ring holds
-// it for the next line).
+// contiguous.  Either every plane of the sweep is kept (J formed afterwards, below), or the plane
+// buffer is updated in place: line a of the previous plane is no longer needed once line a of
+// this plane is computed (the ring holds it for the next line).
 //
 // Vertical faces couple a plane's lines around the periodic box.  Each line's dependence on the
 // line before it has total weight (1 - f_z) e^-dtau <= 1 - f_z, f_z = t |mu_z| / dz < 1, so the walk
@@ -26,10 +26,14 @@
 // (1 - f_z)^W <= 1e-9: the stored lines then carry the periodic solution to far below FP32
 // rounding.  The plane face has no such coupling (W = 0).
 //
-// After each plane the block sums w_d I_d over its directions, in group order, into its J partial
-// (directions with a = x hold their plane transposed, so their tiles pass through shared memory);
-// a second kernel adds the partials of the other groups to J in a fixed order.
+// J = sum_d w_d I_d.  Where the device's memory allows, the sweep keeps every plane of every
+// (wavelength, direction) and one kernel afterwards sums them per point in the tables' direction
+// order (directions with a = x hold their planes transposed, so their tiles pass through shared
+// memory); the sweep's warps then never wait for one another.  Otherwise, after each plane, the
+// block sums w_d I_d over its directions into its J partial, and a second kernel adds the
+// partials of the other groups to J in a fixed order.
 #include <cmath>
+#include <cstdlib>
 #include <vector>
 
 #include "device_common.cuh"
@@ -58,6 +62,7 @@ struct FaceStep {
 
 struct FaceTables {
     FaceDir *d_dirs = nullptr;     // [ndir], grouped
+    int nxd = 0;                   // directions whose lines run along x
     FaceStep *d_steps = nullptr;   // [ndir][nz] by grid direction index, step s = 1 .. nz-1
     int *d_first = nullptr;        // [ngroups + 1]
     int ngroups = 0, wpb = 0, nbpad = 0;
@@ -82,6 +87,7 @@ struct FaceArgs {
     const int *first;
     unsigned *err;
     int nx, ny, nz, nlam, ndir, bc, nbpad;
+    int defer;                     // 1: buf holds every plane [nlam][ndir][nz][np]; J afterwards
 };
 
 enum { R_IK, R_SK, R_AK, R_IU, R_SU, R_AU };
@@ -123,7 +129,10 @@ __global__ void __launch_bounds__(FACE_MAXW * 32, 1) face_sweep_kernel(FaceArgs 
     // S and alpha with this direction's lines contiguous: [nz][na][nb]
     const float *Sl = (D.a_is_x ? a.ST : a.S) + (size_t)lam * npt;
     const float *Al = (D.a_is_x ? a.AT : a.alpha) + (size_t)lam * npt;
-    float *buf = a.buf + ((size_t)lam * a.ndir + D.dir) * np;
+    // this direction's plane buffer (line-major): one plane updated in place, or, when J is
+    // formed after the sweep, every plane (written at plane k, read at the upwind plane ku)
+    float *const bufd = a.buf + ((size_t)lam * a.ndir + D.dir) * np * (a.defer ? (size_t)nz : 1);
+    float *buf = bufd, *bufu = bufd;
     float *ring = sm + (size_t)warp * 12 * a.nbpad;
     float *tile = sm + (size_t)wpb * 12 * a.nbpad;
     float *Jout = (grp == 0 ? a.J : a.Jp + (size_t)(grp - 1) * a.nlam * npt) + (size_t)lam * npt;
@@ -186,16 +195,22 @@ __global__ void __launch_bounds__(FACE_MAXW * 32, 1) face_sweep_kernel(FaceArgs 
                 v = __ldg(a.I_bc + ((size_t)D.dir * a.nlam + lam) * np + (f - (size_t)k0 * np));
             else if (a.bc == RT_BC_THERMAL && up)
                 v = __ldg(Sl + lidx(k0, al, b));
-            buf[m] = v;
+            buf[m + (a.defer ? (size_t)k0 * np : 0)] = v;
             if (Idir) Idir[f] = v;
         }
     }
-    __syncthreads();
-    j_plane(k0);
+    if (!a.defer) {
+        __syncthreads();
+        j_plane(k0);
+    }
 
     const int M = (nb + 31) >> 5;
     for (int s = 1; s < nz; ++s) {
         const int k = up ? s : nz - 1 - s, ku = up ? k - 1 : k + 1;
+        if (a.defer) {
+            buf = bufd + (size_t)k * np;
+            bufu = bufd + (size_t)ku * np;
+        }
         if (active) {
             const FaceStep st = a.steps[(size_t)D.dir * nz + s];
             // line of the m-th step of the walk (m < 0: the lines before the first stored one)
@@ -217,7 +232,7 @@ __global__ void __launch_bounds__(FACE_MAXW * 32, 1) face_sweep_kernel(FaceArgs 
                         const size_t fk = lidx(k, al, b), fu = lidx(ku, al, b);
                         buf5[0][q] = __ldg(Sl + fk);
                         buf5[1][q] = __ldg(Al + fk);
-                        buf5[2][q] = buf[(size_t)al * nb + b];
+                        buf5[2][q] = bufu[(size_t)al * nb + b];
                         buf5[3][q] = __ldg(Sl + fu);
                         buf5[4][q] = __ldg(Al + fu);
                     }
@@ -301,10 +316,53 @@ __global__ void __launch_bounds__(FACE_MAXW * 32, 1) face_sweep_kernel(FaceArgs 
                     if (m + p < na) step(pf[p], m + p);
             }
         }
-        __syncthreads();
-        j_plane(k);
+        if (!a.defer) {
+            __syncthreads();
+            j_plane(k);
+        }
     }
 #undef RING
+}
+
+// J of every point from the directions' planes kept by the sweep: J = sum over the directions in
+// the tables' order of w_d I_d, the planes of directions whose lines run along x transposed
+// through shared memory ([nxd][32][33] per 32 x 32 tile).  One block per (tile, plane, wavelength).
+__global__ void face_j_kernel(const float *__restrict__ vol, float *__restrict__ J,
+                              const FaceDir *__restrict__ dirs, int ndir, int nx, int ny, int nz,
+                              unsigned *err)
+{
+    extern __shared__ float tl[];
+    const int tcx = (nx + 31) >> 5;
+    const int ti = (blockIdx.x % tcx) * 32, tj = (blockIdx.x / tcx) * 32;
+    const int k = blockIdx.y, lam = blockIdx.z;
+    const size_t np = (size_t)nx * ny;
+    int xi = 0;
+    for (int q = 0; q < ndir; ++q) {
+        const FaceDir D = dirs[q];
+        if (!D.a_is_x) continue;
+        const float *pl = vol + (((size_t)lam * ndir + D.dir) * nz + k) * np;   // [x][y]
+        for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+            const int r = e >> 5, c = e & 31, i = ti + r, j = tj + c;
+            tl[(xi * 32 + r) * 33 + c] = (i < nx && j < ny) ? pl[(size_t)i * ny + j] : 0.f;
+        }
+        ++xi;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+        const int r = e >> 5, c = e & 31, i = ti + c, j = tj + r;
+        if (i >= nx || j >= ny) continue;
+        float acc = 0.f;
+        int x2 = 0;
+        for (int q = 0; q < ndir; ++q) {
+            const FaceDir D = dirs[q];
+            const float v = D.a_is_x ? tl[(x2++ * 32 + c) * 33 + r]
+                                     : vol[(((size_t)lam * ndir + D.dir) * nz + k) * np +
+                                           (size_t)j * nx + i];
+            acc = fmaf(D.w, v, acc);
+        }
+        if (!isfinite(acc)) flag_error(err, ERR_NAN);
+        J[((size_t)lam * nz + k) * np + (size_t)j * nx + i] = acc;
+    }
 }
 
 // in [planes][ny][nx] -> out [planes][nx][ny]
@@ -409,6 +467,7 @@ static rt_status face_build(rt_grid *g)
     for (const FaceDir &d : dirs) t->has_x |= d.a_is_x;
     t->ngroups = (int)first.size() - 1;
     t->wpb = wpb;
+    for (const FaceDir &d : dirs) t->nxd += d.a_is_x;
     t->nbpad = (std::max(g->nx, g->ny) + 31) / 32 * 32;
     cudaError_t e = cudaMalloc(&t->d_dirs, dirs.size() * sizeof(FaceDir));
     if (e == cudaSuccess) e = cudaMalloc(&t->d_steps, steps.size() * sizeof(FaceStep));
@@ -439,28 +498,52 @@ static rt_status face_build(rt_grid *g)
     return RT_OK;
 }
 
-// scratch: plane buffers [nlam][ndir][np], J partials [ngroups-1][nlam][npt], and, when some
-// direction's lines run along x, the transposed S and alpha [2][nlam][npt]
-static size_t face_scratch_bytes(const rt_grid *g, int nlam)
+// J after the sweep: the directions' planes of every plane step are kept ([nlam][ndir][npt],
+// 10.5 GB at 128^3 x 52 wavelengths x 24 directions) when that fits a quarter of the device's
+// memory (RT_FACE_VOLUME_MB sets another budget) and the transposed tiles of the directions
+// along x fit the J pass's shared memory; the warps then never wait for one another and one
+// bandwidth-bound pass forms J.  Otherwise each block sums its directions' planes after every
+// plane step.
+static size_t face_j_smem(const FaceTables *t)
+{
+    return (size_t)std::max(t->nxd, 1) * 32 * 33 * sizeof(float);
+}
+
+static bool face_defer(const rt_grid *g, int nlam)
+{
+    if (face_j_smem(g->face) > 200 * 1024) return false;
+    size_t budget = 0, free_b = 0;
+    if (cudaMemGetInfo(&free_b, &budget) != cudaSuccess) return false;
+    budget /= 4;
+    if (const char *e = std::getenv("RT_FACE_VOLUME_MB")) budget = (size_t)std::atoll(e) << 20;
+    return (size_t)nlam * g->ndir * (size_t)g->npt * sizeof(float) <= budget;
+}
+
+// scratch: plane buffers [nlam][ndir][np] and J partials [ngroups-1][nlam][npt] (or, J after the
+// sweep, every plane [nlam][ndir][npt]), and, when some direction's lines run along x, the
+// transposed S and alpha [2][nlam][npt]
+static size_t face_scratch_bytes(const rt_grid *g, int nlam, bool defer)
 {
     const size_t np = (size_t)g->nx * g->ny;
-    return ((size_t)nlam * g->ndir * np +
-            (size_t)(g->face->ngroups - 1 + 2 * g->face->has_x) * nlam * np * g->nz) *
-           sizeof(float);
+    const size_t planes = defer ? (size_t)nlam * g->ndir * np * g->nz
+                                : (size_t)nlam * g->ndir * np +
+                                      (size_t)(g->face->ngroups - 1) * nlam * np * g->nz;
+    return (planes + (size_t)2 * g->face->has_x * nlam * np * g->nz) * sizeof(float);
 }
 
 rt_status face_prepare(rt_grid *g, int nlam)
 {
     void *p;
-    return scratch_get(g, 4, face_scratch_bytes(g, nlam), &p);
+    return scratch_get(g, 4, face_scratch_bytes(g, nlam, face_defer(g, nlam)), &p);
 }
 
 rt_status face_formal_solution(rt_grid *g, int nlam, const float *alpha, const float *S, int bc,
                                const float *I_bc, float *J, float *I_dir, cudaStream_t st)
 {
     const FaceTables *t = g->face;
+    const bool defer = face_defer(g, nlam);
     void *p;
-    RT_TRY(scratch_get(g, 4, face_scratch_bytes(g, nlam), &p));
+    RT_TRY(scratch_get(g, 4, face_scratch_bytes(g, nlam, defer), &p));
     FaceArgs a;
     a.alpha = alpha;
     a.S = S;
@@ -468,10 +551,12 @@ rt_status face_formal_solution(rt_grid *g, int nlam, const float *alpha, const f
     a.I_dir = I_dir;
     a.J = J;
     a.buf = (float *)p;
-    a.Jp = a.buf + (size_t)nlam * g->ndir * g->nx * g->ny;
+    a.defer = defer ? 1 : 0;
+    a.Jp = defer ? nullptr : a.buf + (size_t)nlam * g->ndir * g->nx * g->ny;
     a.ST = a.AT = nullptr;
     if (t->has_x) {
-        float *ST = a.Jp + (size_t)(t->ngroups - 1) * nlam * g->npt;
+        float *ST = defer ? a.buf + (size_t)nlam * g->ndir * g->npt
+                          : a.Jp + (size_t)(t->ngroups - 1) * nlam * g->npt;
         float *AT = ST + (size_t)nlam * g->npt;
         const int nplanes = nlam * g->nz;
         const dim3 tg((g->nx + 31) / 32, (g->ny + 31) / 32, (unsigned)std::min(nplanes, 65535));
@@ -501,7 +586,18 @@ rt_status face_formal_solution(rt_grid *g, int nlam, const float *alpha, const f
     else
         face_sweep_kernel<8><<<grid, 32 * t->wpb, smem, st>>>(a);
     RT_CUDA(cudaGetLastError());
-    if (t->ngroups > 1) {
+    if (defer) {
+        const size_t jsm = face_j_smem(t);
+        if (jsm > 48 * 1024)
+            RT_CUDA(cudaFuncSetAttribute(face_j_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)jsm));
+        const dim3 jg((unsigned)(((g->nx + 31) / 32) * ((g->ny + 31) / 32)), (unsigned)g->nz,
+                      (unsigned)nlam);
+        note_launch();
+        face_j_kernel<<<jg, 256, jsm, st>>>(a.buf, J, t->d_dirs, g->ndir, g->nx, g->ny, g->nz,
+                                            g->d_err);
+        RT_CUDA(cudaGetLastError());
+    } else if (t->ngroups > 1) {
         note_launch();
         face_sum_kernel<<<1216, 256, 0, st>>>(J, a.Jp, t->ngroups - 1, (size_t)nlam * g->npt);
         RT_CUDA(cudaGetLastError());

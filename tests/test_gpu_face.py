@@ -32,11 +32,15 @@ def _vertical_face_steps(z, dirs, dx, dy):
     return n
 
 
+@pytest.mark.parametrize("jmode", ["after_sweep", "per_plane"])
 @pytest.mark.parametrize("bc", [0, 1, 2])
-def test_ragged_random_multi_lambda(rt, bc):
+def test_ragged_random_multi_lambda(rt, monkeypatch, bc, jmode):
     """37 x 23 points (neither a multiple of the warp), non-uniform z with both kinds of face,
     lines along x for some rays and along y for others, optical depths per step from 1e-6 to 1e3,
-    three wavelengths, every boundary condition; J and every directional intensity."""
+    three wavelengths, every boundary condition; J and every directional intensity.  J formed
+    after the sweep from every plane kept (the default where memory allows) and, with a zero
+    memory budget for that, per plane step by each block."""
+    monkeypatch.setenv("RT_FACE_VOLUME_MB", "0" if jmode == "per_plane" else "100000")
     rng = np.random.default_rng(21)
     nx, ny, nz, nlam = 37, 23, 19, 3
     dx, dy = 0.7, 0.9
@@ -56,9 +60,12 @@ def test_ragged_random_multi_lambda(rt, bc):
     assert_parity(I.cpu().numpy(), Ir, what="I")
 
 
-def test_thin_layers_close_the_periodic_cycle(rt):
+@pytest.mark.parametrize("jmode", ["after_sweep", "per_plane"])
+def test_thin_layers_close_the_periodic_cycle(rt, monkeypatch, jmode):
     """Planes far apart (f_z about 0.1): the same-plane chain runs around the box several times,
-    and the walk before the first stored line is long; optically thin, so nothing damps it."""
+    and the walk before the first stored line is long; optically thin, so nothing damps it.  J
+    after the sweep and per plane step."""
+    monkeypatch.setenv("RT_FACE_VOLUME_MB", "0" if jmode == "per_plane" else "100000")
     nx, ny, nz = 20, 16, 6
     z = np.arange(nz) * 4.0
     dirs, w = s4_quadrature()
