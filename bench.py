@@ -55,8 +55,8 @@ PROFILED = {"sc_pipe_kernel": {"file": "paper_2306_01041_gb300/csrc/regular_pipe
                                    # per update, scaled to the launch by its updates
                                    "dram_bytes_per_update": (1.350062e9 + 0.619866e9) / 146.016e6},
             "face_sweep_kernel": {"file": "paper_2306_01041_gb300/csrc/regular_face.cu",
-                                  "sha1": "114bbcaf3b977a2a3bf46d055c187729ecde7920",
-                                  "dram_bytes_per_launch": 21.764292352e9 + 11.011950592e9}}
+                                  "sha1": "09789e460a0a787c6dc7550acd0ed83fea06e619",
+                                  "dram_bytes_per_launch": 25.295442176e9 + 10.433180160e9}}
 
 # Algorithmic FP32 work of one point-direction-wavelength update of the regular sweep, counted in
 # lane operations (an FMA counts once): three bilinear interpolations (6 each), dtau (2), interval

@@ -326,42 +326,98 @@ __global__ void __launch_bounds__(FACE_MAXW * 32, 1) face_sweep_kernel(FaceArgs 
 
 // J of every point from the directions' planes kept by the sweep: J = sum over the directions in
 // the tables' order of w_d I_d, the planes of directions whose lines run along x transposed
-// through shared memory ([nxd][32][33] per 32 x 32 tile).  One block per (tile, plane, wavelength).
-__global__ void face_j_kernel(const float *__restrict__ vol, float *__restrict__ J,
-                              const FaceDir *__restrict__ dirs, int ndir, int nx, int ny, int nz,
-                              unsigned *err)
+// through shared memory ([nxd][32][33] per 32 x 32 tile).  One block per (tile, plane, wavelength),
+// FJ_PTS points a thread.  Every direction's source is addressed through one generic pointer (a
+// global plane or a shared tile), so that the loop over directions has no branch and the loads
+// of several directions are in flight at once.
+constexpr int FJ_THREADS = 256, FJ_PTS = 1024 / FJ_THREADS;
+
+__global__ void __launch_bounds__(FJ_THREADS) face_j_kernel(const float *__restrict__ vol,
+                                                            float *__restrict__ J,
+                                                            const FaceDir *__restrict__ dirs,
+                                                            int ndir, int nx, int ny, int nz,
+                                                            unsigned *err)
 {
     extern __shared__ float tl[];
+    __shared__ const float *src[MAX_DIR];   // the direction's plane, or its transposed tile
+    __shared__ float wq[MAX_DIR];
+    __shared__ const float *xpl[MAX_DIR];   // the planes held as [x][y], by tile slot
+    __shared__ int isx[MAX_DIR];
+    __shared__ int nxd;
     const int tcx = (nx + 31) >> 5;
     const int ti = (blockIdx.x % tcx) * 32, tj = (blockIdx.x / tcx) * 32;
     const int k = blockIdx.y, lam = blockIdx.z;
     const size_t np = (size_t)nx * ny;
-    int xi = 0;
-    for (int q = 0; q < ndir; ++q) {
-        const FaceDir D = dirs[q];
-        if (!D.a_is_x) continue;
-        const float *pl = vol + (((size_t)lam * ndir + D.dir) * nz + k) * np;   // [x][y]
-        for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
-            const int r = e >> 5, c = e & 31, i = ti + r, j = tj + c;
-            tl[(xi * 32 + r) * 33 + c] = (i < nx && j < ny) ? pl[(size_t)i * ny + j] : 0.f;
+    // the direction table, set up by the first warp (two directions a lane, MAX_DIR = 64): a
+    // direction's tile slot is the number of directions along x before it in the table
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        unsigned bal[2];
+        FaceDir D[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int q = lane + 32 * h;
+            if (q < ndir) D[h] = dirs[q];
+            bal[h] = __ballot_sync(0xffffffffu, q < ndir && D[h].a_is_x);
         }
-        ++xi;
+        const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int q = lane + 32 * h;
+            if (q >= ndir) continue;
+            const float *pl = vol + (((size_t)lam * ndir + D[h].dir) * nz + k) * np;
+            wq[q] = D[h].w;
+            isx[q] = D[h].a_is_x;
+            if (D[h].a_is_x) {
+                const int xi = (h ? __popc(bal[0]) : 0) + __popc(bal[h] & lt);
+                xpl[xi] = pl;
+                src[q] = tl + xi * 32 * 33;
+            } else {
+                src[q] = pl;
+            }
+        }
+        if (lane == 0) nxd = __popc(bal[0]) + __popc(bal[1]);
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
-        const int r = e >> 5, c = e & 31, i = ti + c, j = tj + r;
-        if (i >= nx || j >= ny) continue;
-        float acc = 0.f;
-        int x2 = 0;
-        for (int q = 0; q < ndir; ++q) {
-            const FaceDir D = dirs[q];
-            const float v = D.a_is_x ? tl[(x2++ * 32 + c) * 33 + r]
-                                     : vol[(((size_t)lam * ndir + D.dir) * nz + k) * np +
-                                           (size_t)j * nx + i];
-            acc = fmaf(D.w, v, acc);
+    // stage the planes held as [x][y], transposed
+#pragma unroll 2
+    for (int xi = 0; xi < nxd; ++xi) {
+        const float *pl = xpl[xi];
+#pragma unroll
+        for (int u = 0; u < FJ_PTS; ++u) {
+            const int e = threadIdx.x + FJ_THREADS * u, r = e >> 5, c = e & 31;
+            const int i = ti + r, j = tj + c;
+            tl[(xi * 32 + r) * 33 + c] = (i < nx && j < ny) ? pl[(size_t)i * ny + j] : 0.f;
         }
-        if (!isfinite(acc)) flag_error(err, ERR_NAN);
-        J[((size_t)lam * nz + k) * np + (size_t)j * nx + i] = acc;
+    }
+    __syncthreads();
+    // per point: offset in a [y][x] plane (clamped into the plane) and in a transposed tile
+    size_t goff[FJ_PTS];
+    int toff[FJ_PTS];
+    float acc[FJ_PTS];
+#pragma unroll
+    for (int u = 0; u < FJ_PTS; ++u) {
+        const int e = threadIdx.x + FJ_THREADS * u, r = e >> 5, c = e & 31;
+        const int i = min(ti + c, nx - 1), j = min(tj + r, ny - 1);
+        goff[u] = (size_t)j * nx + i;
+        toff[u] = c * 33 + r;
+        acc[u] = 0.f;
+    }
+#pragma unroll 2
+    for (int q = 0; q < ndir; ++q) {
+        const float *b = src[q];
+        const bool x = isx[q];
+        const float w = wq[q];
+#pragma unroll
+        for (int u = 0; u < FJ_PTS; ++u) acc[u] = fmaf(w, b[x ? (size_t)toff[u] : goff[u]], acc[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < FJ_PTS; ++u) {
+        const int e = threadIdx.x + FJ_THREADS * u, r = e >> 5, c = e & 31;
+        const int i = ti + c, j = tj + r;
+        if (i >= nx || j >= ny) continue;
+        if (!isfinite(acc[u])) flag_error(err, ERR_NAN);
+        J[((size_t)lam * nz + k) * np + (size_t)j * nx + i] = acc[u];
     }
 }
 
@@ -511,7 +567,7 @@ static size_t face_j_smem(const FaceTables *t)
 
 static bool face_defer(const rt_grid *g, int nlam)
 {
-    if (face_j_smem(g->face) > 200 * 1024) return false;
+    if (face_j_smem(g->face) > 200 * 1024 || nlam > 65535 || g->nz > 65535) return false;
     size_t budget = 0, free_b = 0;
     if (cudaMemGetInfo(&free_b, &budget) != cudaSuccess) return false;
     budget /= 4;
