@@ -129,6 +129,10 @@ rt_status rt_grid_top_points(rt_grid_t grid, int64_t *idx);
  * The scheme applies to rt_formal_solution and so to the Lambda iterations; rt_lambda_star,
  * rt_emergent_intensity and the adjoint stay plane to plane.  RT_SC_FACE needs periodic sides and
  * nx, ny <= 256; its tables (per direction and plane) are built on first selection (synchronous).
+ * Its formal solution keeps every plane of every (wavelength, direction) in the grid's scratch
+ * (nlam * ndir * npt floats) and forms J from them afterwards when that fits a quarter of the
+ * device's memory (the environment variable RT_FACE_VOLUME_MB sets another limit), else it sums J
+ * after every plane step; both give J to FP32 rounding of the same sum.
  * RT_EINVAL for a Voronoi grid, closed sides, larger planes, or planes so far apart that the
  * cycle would need more than 16 laps of the box to close. */
 enum rt_sc_scheme { RT_SC_PLANE = 0, RT_SC_FACE = 1 };
