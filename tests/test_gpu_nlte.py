@@ -26,10 +26,10 @@ def rt():
 
 
 @functools.lru_cache(maxsize=None)
-def _setup(nx, ny, nz):
+def _setup(nx, ny, nz, n_line=50):
     atm = make_atmosphere(0)
     f, ax = regular_fields(nx, ny, nz, atm)
-    data = model_atom(np.min(f["ne"] / np.sqrt(f["T"])))
+    data = model_atom(np.min(f["ne"] / np.sqrt(f["T"])), n_line=n_line)
     return atm, f, ax, data
 
 
@@ -48,30 +48,37 @@ def test_lte_populations(rt):
                   floor=0.0, what="LTE pops")
 
 
+# (grid, line nodes): 52 nodes on 2880 points (a whole number of 32-point blocks), and 112 nodes
+# (four per lane of a warp) on 2990 points (a ragged last block)
+ATOM_CASES = [((12, 10, 24), 50), ((13, 10, 23), 110)]
+
+
+@pytest.mark.parametrize("shape,n_line", ATOM_CASES)
 @pytest.mark.parametrize("perturb", [0.0, 0.3])
-def test_source_terms(rt, perturb):
-    """alpha, S at all 52 nodes (Voigt line profile on the GPU vs scipy's in the oracle)."""
-    atm, f, (x, y, z, dx, dy), data = _setup(12, 10, 24)
+def test_source_terms(rt, perturb, shape, n_line):
+    """alpha, S at every node (Voigt line profile on the GPU vs scipy's in the oracle)."""
+    atm, f, (x, y, z, dx, dy), data = _setup(*shape, n_line)
     A = Atom(data, atm.kappa0)
     rng = np.random.default_rng(2)
     pops = A.lte_pops(f["T"], f["ne"], f["nH"]) * np.exp(perturb * rng.standard_normal((3, f["T"].size)))
     dirs, w = s4_quadrature()
-    g = rt.RegularGrid(12, 10, 24, dx, dy, z, dirs, w)
+    g = rt.RegularGrid(*shape, dx, dy, z, dirs, w)
     alpha, S = rt.source_terms(g, rt.Atom(data, atm.kappa0), _gpu_atm(rt, f), to_gpu(pops))
     ar, sr = A.alpha_S(f["T"], f["rho"], f["ne"], pops.astype(np.float32).astype(np.float64))
     assert_parity(alpha.cpu().numpy(), ar, rel=2e-5, floor=0.0, what="alpha")
     assert_parity(S.cpu().numpy(), sr, rel=2e-5, floor=0.0, what="S")
 
 
-def test_statistical_equilibrium(rt):
-    atm, f, (x, y, z, dx, dy), data = _setup(12, 10, 24)
+@pytest.mark.parametrize("shape,n_line", ATOM_CASES)
+def test_statistical_equilibrium(rt, shape, n_line):
+    atm, f, (x, y, z, dx, dy), data = _setup(*shape, n_line)
     A = Atom(data, atm.kappa0)
     dirs, w = s4_quadrature()
     pops = A.lte_pops(f["T"], f["ne"], f["nH"])
     alpha, S = A.alpha_S(f["T"], f["rho"], f["ne"], pops)
-    J = OrcRegular(12, 10, 24, dx, dy, z, dirs, w).formal_solution(alpha, S)
+    J = OrcRegular(*shape, dx, dy, z, dirs, w).formal_solution(alpha, S)
     new = A.statistical_equilibrium(A.rate_matrix(f["T"], f["ne"], J), f["nH"])
-    g = rt.RegularGrid(12, 10, 24, dx, dy, z, dirs, w)
+    g = rt.RegularGrid(*shape, dx, dy, z, dirs, w)
     p = to_gpu(pops)
     dmax = rt.statistical_equilibrium(g, rt.Atom(data, atm.kappa0), _gpu_atm(rt, f), to_gpu(J), p)
     assert_parity(p.cpu().numpy(), new, rel=5e-5, floor=0.0, what="pops")
